@@ -1,0 +1,209 @@
+/*
+ * fgfrft.h -- C ABI of libfgfrft, the GB300 (sm_103a) online hot path of the
+ * fast graph fractional Fourier transform (FGFRFT).
+ *
+ * Method (paper: "FGFRFT: Fast Graph Fractional Fourier Transform via Exact
+ * Spectral Splitting and Fourier-Series Approximation"):
+ *
+ *   F        unitary N x N graph Fourier matrix (Sec. III-A), eigenphases
+ *            theta_k in (-pi, pi].
+ *   P        orthogonal projector onto the lambda = -1 eigenspace, P_c = I - P
+ *            (Sec. III-B).
+ *   M_l      = F^l P_c for l = -L..L, the cached integer powers (Algorithm 1,
+ *            offline part; M_{-l} = M_l^H by Prop. 2 / Eq. "eqefficient_computation").
+ *   c_l(a)   = sin(pi (a - l)) / (pi (a - l)) (Sec. III-A).
+ *   Q_L^a    = e^{j pi a} P + sum_{l=-L}^{L} c_l(a) M_l        (Def. 1)
+ *   Y        = Q_L^a X, one order per signal column              (Def. 2)
+ *   dY/da    = j pi e^{j pi a} P X + sum_l c_l'(a) M_l X          (Prop. 3)
+ *   Q^H G    = Q_L^{-a} G                                         (Prop. 2)
+ *
+ * Conventions shared by every call:
+ *   - Matrices are row-major.  "c64" means interleaved complex float32
+ *     (re, im) pairs, "c128" interleaved complex float64.
+ *   - Signals are stored one per row: X[j * N + i] is entry i of signal j
+ *     (column j of the N x B matrix X).  Y, dY/da, G and gradX use the same
+ *     layout.
+ *   - Every pointer named *_dev is device memory owned by the caller; *_host
+ *     is host memory read before the call returns.  The library allocates no
+ *     device memory: the plan lives in caller memory of fgfrft_plan_bytes()
+ *     bytes, scratch in a caller buffer of fgfrft_work_bytes() bytes.
+ *   - Device memory passed to one call must not overlap between inputs and
+ *     outputs.  A work buffer may be reused by the next call on the same
+ *     stream, not by concurrent calls.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work on it and return without synchronising,
+ *     except fgfrft_precompute (which reads reductions back) and
+ *     fgfrft_plan_status.
+ *   - Argument errors are detected on the host before anything is enqueued.
+ *     CUDA launch errors return FGFRFT_ERR_CUDA.  Errors found by kernels
+ *     (a bounded wait that ran out) are recorded in the plan's device status
+ *     word and reported by fgfrft_plan_status.
+ *   - Orders are host float64.  An order a is an integer iff a == round(a);
+ *     then c_l(a) is the Kronecker delta and Q = F^a exactly (Remark 2), which
+ *     the stored powers cover only for |a| <= L: larger integer orders return
+ *     FGFRFT_ERR_UNSUPPORTED.
+ *   - L (0 <= L <= L_max) selects the central blocks -L..L of the stored stack.
+ */
+#ifndef FGFRFT_H
+#define FGFRFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fgfrft_plan_s* fgfrft_plan;
+
+enum fgfrft_status {
+  FGFRFT_OK = 0,
+  FGFRFT_ERR_INVALID_ARG = 1,        /* bad size, NULL pointer, short buffer, NaN order */
+  FGFRFT_ERR_UNSUPPORTED = 2,        /* integer |a| > L, L > L_max, storage missing for a path */
+  FGFRFT_ERR_NOT_UNITARY = 3,        /* ||F^H F - I||_F / sqrt(N) above 1e-8 */
+  FGFRFT_ERR_AMBIGUOUS_SPECTRUM = 4, /* an eigenvalue too close to -1 to classify in FP64 */
+  FGFRFT_ERR_NO_MEMORY = 5,          /* host allocation of the plan record failed */
+  FGFRFT_ERR_CUDA = 6,               /* a CUDA call or kernel launch failed */
+  FGFRFT_ERR_TIMEOUT = 7,            /* a kernel's bounded wait ran out (status word) */
+};
+
+/* Storage of the power stack, a bit set passed to fgfrft_precompute. */
+enum fgfrft_storage {
+  FGFRFT_STORE_C64 = 1,       /* blocks as c64, 8 B per entry: assembly and FP32 paths */
+  FGFRFT_STORE_SPLIT_F16 = 2, /* blocks as four fp16 planes {re_hi, re_lo, im_hi, im_lo}
+                                 of the entries scaled by 2^12, 8 B per entry:
+                                 tensor-core paths */
+};
+
+/* Flags of fgfrft_apply / fgfrft_grad. */
+enum fgfrft_flags {
+  FGFRFT_ADJOINT = 1,             /* apply (Q_L^a)^H = Q_L^{-a} (Prop. 2) */
+  FGFRFT_SHARED_ALPHA = 2,        /* alpha_host holds one order used by every column */
+  FGFRFT_PATH_PLAIN = 0x10,       /* per order: assemble Q (c64), then FP32 SIMT GEMM */
+  FGFRFT_PATH_ASSEMBLED = 0x20,   /* all orders assembled in one pass into split-fp16
+                                     operators, then one tensor-core GEMM over groups */
+  FGFRFT_PATH_STACKED = 0x40,     /* no assembly: the stacked powers [M_-L..M_L, P] as one
+                                     tensor-core GEMM against X, per-column orders */
+  FGFRFT_PATH_STACKED_FP32 = 0x80 /* the stacked form on FP32 CUDA cores */
+};
+#define FGFRFT_PATH_MASK 0xF0
+
+/* Operation codes of fgfrft_work_bytes. */
+enum fgfrft_op { FGFRFT_OP_ASSEMBLE = 1, FGFRFT_OP_APPLY = 2, FGFRFT_OP_GRAD = 3 };
+
+/* Human-readable name of a status code; never NULL. */
+const char* fgfrft_strerror(int status);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int fgfrft_version(void);
+
+/* Bytes of device memory a plan for (N, L_max, storage) occupies: the status
+ * word, 2 L_max + 2 blocks of N x N entries (M_{-L_max} .. M_{L_max}, then P)
+ * in every storage requested, each block padded to 256 B.  Returns 0 for
+ * invalid arguments (N < 1, L_max < 0, no known storage bit). */
+size_t fgfrft_plan_bytes(int64_t N, int L_max, int storage);
+
+/* Bytes of FP64 device scratch fgfrft_precompute needs: 3 N^2 complex128
+ * matrices plus a reduction area. */
+size_t fgfrft_precompute_work_bytes(int64_t N);
+
+/*
+ * Offline part of Algorithm 1, in FP64 on the GPU.
+ *   F_dev       N x N complex128 (c128) row-major unitary matrix, device.
+ *   L_max       highest stored power (>= 0).
+ *   storage     bit set of enum fgfrft_storage.
+ *   W_dev       optional N x r complex128 row-major matrix with orthonormal
+ *               columns spanning the lambda = -1 eigenspace (Algorithm 1,
+ *               "form W"); NULL lets the library find the eigenspace itself:
+ *               S = (I - F)(I - F)^H / 4 has eigenvalues sin^2(theta_k / 2),
+ *               equal to 1 exactly on the lambda = -1 eigenspace; repeated
+ *               squaring of S followed by McWeeny purification P <- 3P^2 - 2P^3
+ *               gives P.  Eigenvalues within ~3e-8 of -1 count as -1; one
+ *               that squaring cannot separate in 46 steps gives
+ *               FGFRFT_ERR_AMBIGUOUS_SPECTRUM.
+ *   r_W         number of columns of W_dev (ignored when W_dev is NULL).
+ *   plan_mem    device buffer of at least fgfrft_plan_bytes(N, L_max, storage)
+ *               bytes, 256-byte aligned; it holds the plan for its lifetime.
+ *   work        device scratch of fgfrft_precompute_work_bytes(N) bytes,
+ *               256-byte aligned; free again when the call returns.
+ *   out         receives the plan handle (a small host record; release it
+ *               with fgfrft_plan_destroy).
+ * Checks ||F^H F - I||_F / sqrt(N) <= 1e-8 (FGFRFT_ERR_NOT_UNITARY).
+ * Synchronises the stream (it reads traces back to the host).
+ */
+int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage,
+                      const double* W_dev, int64_t r_W,
+                      void* plan_mem, size_t plan_bytes,
+                      void* work, size_t work_bytes,
+                      void* stream, fgfrft_plan* out);
+
+/* Plan metadata; any output pointer may be NULL.
+ *   r_neg1         rank of P (the multiplicity of lambda = -1).
+ *   proj_residual  ||F P + P||_F after precompute (0 when r_neg1 = 0).
+ *   squarings      squaring steps the projector needed (0 when W was given). */
+int fgfrft_plan_info(fgfrft_plan p, int64_t* N, int* L_max, int* storage, int* r_neg1,
+                     double* proj_residual, int* squarings, size_t* plan_bytes);
+
+/* Device pointer to stored block l (-L_max <= l <= L_max, or l = L_max + 1 for
+ * P) in the given storage (one bit), and the element stride between blocks.
+ * For FGFRFT_STORE_C64 the block is N x N c64; for FGFRFT_STORE_SPLIT_F16 it is
+ * four consecutive N x N fp16 planes.  NULL if absent. */
+const void* fgfrft_plan_block(fgfrft_plan p, int storage, int l, int64_t* block_stride_elems);
+
+/* Synchronise the stream, read the plan's device status word and clear it:
+ * FGFRFT_OK, or FGFRFT_ERR_TIMEOUT when a kernel's bounded wait ran out. */
+int fgfrft_plan_status(fgfrft_plan p, void* stream);
+
+/* Release the host record of a plan.  Frees nothing caller-owned. */
+int fgfrft_plan_destroy(fgfrft_plan p);
+
+/* Bytes of scratch an online call needs (op = enum fgfrft_op).  count is A
+ * for FGFRFT_OP_ASSEMBLE and B otherwise; alpha_host is needed because the
+ * assembled path sizes its scratch by the number of distinct orders. */
+size_t fgfrft_work_bytes(fgfrft_plan p, int op, const double* alpha_host, int64_t count,
+                         int L, int flags);
+
+/*
+ * Online part of Algorithm 1 (Def. 1), A orders in one pass over the stack.
+ *   alpha_host  A orders.
+ *   Q_dev       A x N x N c64 output, Q_dev[a][i][k] = (Q_L^{alpha_a})_{ik}.
+ * A = 1 streams the 2L + 2 stored blocks once with bulk-copy staging; A > 1
+ * reads each stored entry once for all A outputs.  Needs FGFRFT_STORE_C64.
+ */
+int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L,
+                    void* Q_dev, void* work, size_t work_bytes, void* stream);
+
+/*
+ * Y[:, j] = Q_L^{alpha_j} X[:, j] for j = 0..B-1 (Def. 2), or (Q_L^{alpha_j})^H X[:, j]
+ * with FGFRFT_ADJOINT.
+ *   alpha_host  B orders, or 1 with FGFRFT_SHARED_ALPHA.
+ *   X_dev, Y_dev  B x N c64 (signal j at offset j * N).
+ * Path: the FGFRFT_PATH_* bit in flags, else chosen by the library: columns
+ * are grouped into runs of equal order; runs of at least 64 columns use
+ * FGFRFT_PATH_ASSEMBLED, otherwise FGFRFT_PATH_STACKED (tensor paths need
+ * FGFRFT_STORE_SPLIT_F16, else the FP32 paths are used).
+ */
+int fgfrft_apply(fgfrft_plan p, const double* alpha_host, int64_t B, int L,
+                 const void* X_dev, void* Y_dev, int flags,
+                 void* work, size_t work_bytes, void* stream);
+
+/*
+ * Forward with dual accumulators and the backward of Y = Q_L^{alpha_j} X[:, j].
+ * Forward (X_dev != NULL): Y (if Y_dev) and D = dY/dalpha (if dY_dev, Prop. 3)
+ *   from the same pass over the stored powers.
+ * Backward (G_dev != NULL), G = dloss/dRe(Y) + j dloss/dIm(Y):
+ *   gradX = (Q_L^{alpha_j})^H G[:, j] (if gradX_dev; Prop. 2), and
+ *   gradalpha[j] = Re sum_i conj(G_ij) D_ij (if gradalpha_dev), with D read
+ *   from dY_dev (computed in this call or an earlier one).
+ * Paths: FGFRFT_PATH_STACKED (default with FGFRFT_STORE_SPLIT_F16) or
+ * FGFRFT_PATH_STACKED_FP32.
+ */
+int fgfrft_grad(fgfrft_plan p, const double* alpha_host, int64_t B, int L,
+                const void* X_dev, void* Y_dev, void* dY_dev,
+                const void* G_dev, void* gradX_dev, float* gradalpha_dev,
+                int flags, void* work, size_t work_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FGFRFT_H */

@@ -1,0 +1,598 @@
+// Host side of the C ABI declared in include/fgfrft.h: argument checks, plan
+// layout, the offline driver (Algorithm 1, offline part) and the dispatch of the
+// online calls (Def. 1, Def. 2, Props. 2-3) onto the kernels.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "tc.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct Layout {
+  int64_t blk_elems, Np, plane_elems;
+  size_t off_c64, off_f16, total;
+};
+
+Layout plan_layout(int64_t N, int L_max, int storage) {
+  Layout l{};
+  const int nblk = 2 * L_max + 2;
+  l.blk_elems = round_up(N * N, 32);
+  l.Np = round_up(N, 8);
+  l.plane_elems = round_up(N * l.Np, 128);
+  size_t off = kAlign;  // status word area
+  l.off_c64 = off;
+  if (storage & FGFRFT_STORE_C64) off = align_up(off + (size_t)nblk * l.blk_elems * sizeof(float2));
+  l.off_f16 = off;
+  if (storage & FGFRFT_STORE_SPLIT_F16) off = align_up(off + (size_t)nblk * 4 * l.plane_elems * sizeof(__half));
+  l.total = off;
+  return l;
+}
+
+inline bool aligned(const void* p, size_t a = kAlign) { return ((uintptr_t)p % a) == 0; }
+
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return FGFRFT_ERR_CUDA; \
+  } while (0)
+
+// Host copy of the orders, validated.  Returns FGFRFT_OK or an error code.
+int gather_orders(const double* alpha_host, int64_t B, int L, int flags, std::vector<double>& out) {
+  if (!alpha_host || B < 1) return FGFRFT_ERR_INVALID_ARG;
+  out.resize((size_t)B);
+  const bool shared = (flags & FGFRFT_SHARED_ALPHA) != 0;
+  for (int64_t j = 0; j < B; ++j) {
+    const double a = shared ? alpha_host[0] : alpha_host[j];
+    if (!isfinite(a)) return FGFRFT_ERR_INVALID_ARG;
+    if (a == nearbyint(a) && fabs(a) > (double)L) return FGFRFT_ERR_UNSUPPORTED;
+    out[(size_t)j] = a;
+  }
+  return FGFRFT_OK;
+}
+
+// Runs of equal orders: (start, length).
+std::vector<std::pair<int64_t, int64_t>> order_runs(const std::vector<double>& a) {
+  std::vector<std::pair<int64_t, int64_t>> runs;
+  int64_t s = 0;
+  for (int64_t j = 1; j <= (int64_t)a.size(); ++j) {
+    if (j == (int64_t)a.size() || a[(size_t)j] != a[(size_t)s]) {
+      runs.push_back({s, j - s});
+      s = j;
+    }
+  }
+  return runs;
+}
+
+// Sequential sub-allocator over a caller work buffer (nullptr base = sizing only).
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off = align_up(off + count * sizeof(T));
+    return p;
+  }
+};
+
+constexpr int kAssembledMinRun = 64;
+
+int choose_path(const fgfrft_plan_s* p, const std::vector<double>& a, int flags) {
+  int path = flags & FGFRFT_PATH_MASK;
+  if (path) return path;
+  const bool tensor = (p->storage & FGFRFT_STORE_SPLIT_F16) != 0 && fg_tc_available();
+  auto runs = order_runs(a);
+  int64_t min_run = INT64_MAX;
+  for (auto& r : runs) min_run = std::min(min_run, r.second);
+  if (min_run >= kAssembledMinRun) {
+    if (tensor) return FGFRFT_PATH_ASSEMBLED;
+    return (p->storage & FGFRFT_STORE_C64) ? FGFRFT_PATH_PLAIN : FGFRFT_PATH_STACKED_FP32;
+  }
+  return tensor ? FGFRFT_PATH_STACKED : FGFRFT_PATH_STACKED_FP32;
+}
+
+// Work layout of an apply / grad call; base == nullptr computes the size only.
+struct ApplyWork {
+  double* alpha_dev = nullptr;
+  double* group_alpha_dev = nullptr;
+  float2* coef = nullptr;
+  float2* coefd = nullptr;
+  float2* Qc = nullptr;
+  __half* Qs = nullptr;
+  __half* Xs = nullptr;
+  int* col_exp = nullptr;
+  double* partials = nullptr;
+  void* tc_scratch = nullptr;
+  size_t tc_scratch_bytes = 0;
+  int64_t xs_rows = 0;
+  size_t bytes = 0;
+};
+
+ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int path, int64_t groups, bool grad) {
+  ApplyWork w;
+  Carve c{base};
+  const int nb = 2 * L + 2;
+  w.alpha_dev = c.take<double>((size_t)B);
+  switch (path) {
+    case FGFRFT_PATH_PLAIN:
+      w.group_alpha_dev = c.take<double>((size_t)groups);
+      w.coef = c.take<float2>((size_t)nb * groups);
+      w.Qc = c.take<float2>((size_t)p->N * p->N);
+      break;
+    case FGFRFT_PATH_STACKED_FP32:
+      w.coef = c.take<float2>((size_t)nb * B);
+      w.coefd = c.take<float2>((size_t)nb * B);
+      break;
+    case FGFRFT_PATH_ASSEMBLED:
+      w.group_alpha_dev = c.take<double>((size_t)groups);
+      w.coef = c.take<float2>((size_t)nb * groups);
+      w.Qs = c.take<__half>((size_t)groups * 4 * p->plane_elems);
+      w.xs_rows = fg_tc_signal_rows(B, groups);
+      w.Xs = c.take<__half>((size_t)4 * w.xs_rows * p->Np);
+      w.col_exp = c.take<int>((size_t)w.xs_rows);
+      w.tc_scratch_bytes = fg_tc_scratch_bytes(p->N, B, groups, 1);
+      w.tc_scratch = c.take<char>(w.tc_scratch_bytes);
+      break;
+    case FGFRFT_PATH_STACKED:
+      w.coef = c.take<float2>((size_t)nb * B);
+      w.coefd = c.take<float2>((size_t)nb * B);
+      w.xs_rows = fg_tc_signal_rows(B, 1);
+      w.Xs = c.take<__half>((size_t)4 * w.xs_rows * p->Np);
+      w.col_exp = c.take<int>((size_t)w.xs_rows);
+      w.tc_scratch_bytes = fg_tc_scratch_bytes(p->N, B, 1, nb);
+      w.tc_scratch = c.take<char>(w.tc_scratch_bytes);
+      break;
+    default:
+      break;
+  }
+  if (grad) w.partials = c.take<double>((size_t)B * fg_grad_chunks(p->N));
+  w.bytes = c.off;
+  return w;
+}
+
+const char* kStatusNames[] = {
+    "FGFRFT_OK",
+    "FGFRFT_ERR_INVALID_ARG: invalid argument",
+    "FGFRFT_ERR_UNSUPPORTED: unsupported request (integer order beyond L, L > L_max, or storage missing)",
+    "FGFRFT_ERR_NOT_UNITARY: F is not unitary to 1e-8",
+    "FGFRFT_ERR_AMBIGUOUS_SPECTRUM: an eigenvalue of F is too close to -1 to classify",
+    "FGFRFT_ERR_NO_MEMORY: host allocation failed",
+    "FGFRFT_ERR_CUDA: a CUDA call failed",
+    "FGFRFT_ERR_TIMEOUT: a bounded device wait ran out",
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* fgfrft_strerror(int status) {
+  if (status < 0 || status > FGFRFT_ERR_TIMEOUT) return "unknown fgfrft status";
+  return kStatusNames[status];
+}
+
+int fgfrft_version(void) { return 100; }
+
+size_t fgfrft_plan_bytes(int64_t N, int L_max, int storage) {
+  if (N < 1 || N > 65536 || L_max < 0 || L_max > 1000) return 0;
+  if ((storage & (FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16)) == 0) return 0;
+  if (storage & ~(FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16)) return 0;
+  return plan_layout(N, L_max, storage).total;
+}
+
+size_t fgfrft_precompute_work_bytes(int64_t N) {
+  if (N < 1 || N > 65536) return 0;
+  return align_up((size_t)3 * N * N * sizeof(double2)) + kAlign;
+}
+
+int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, const double* W_dev, int64_t r_W,
+                      void* plan_mem, size_t plan_bytes, void* work, size_t work_bytes, void* stream,
+                      fgfrft_plan* out) {
+  if (!out) return FGFRFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  const size_t need = fgfrft_plan_bytes(N, L_max, storage);
+  if (need == 0 || !F_dev || !plan_mem || !work || plan_bytes < need) return FGFRFT_ERR_INVALID_ARG;
+  if (work_bytes < fgfrft_precompute_work_bytes(N)) return FGFRFT_ERR_INVALID_ARG;
+  if (!aligned(plan_mem) || !aligned(work) || !aligned(F_dev, 16)) return FGFRFT_ERR_INVALID_ARG;
+  if (W_dev && (r_W < 0 || r_W > N || !aligned(W_dev, 16))) return FGFRFT_ERR_INVALID_ARG;
+  if (N > 46340) return FGFRFT_ERR_UNSUPPORTED;  // int GEMM indices
+  cudaStream_t s = (cudaStream_t)stream;
+  const Layout lay = plan_layout(N, L_max, storage);
+  fgfrft_plan_s* p = (fgfrft_plan_s*)calloc(1, sizeof(fgfrft_plan_s));
+  if (!p) return FGFRFT_ERR_NO_MEMORY;
+  p->N = N;
+  p->L_max = L_max;
+  p->storage = storage;
+  p->nblk = 2 * L_max + 2;
+  p->blk_elems = lay.blk_elems;
+  p->Np = lay.Np;
+  p->plane_elems = lay.plane_elems;
+  p->bytes = need;
+  char* pm = (char*)plan_mem;
+  p->dstatus = (uint32_t*)pm;
+  p->c64 = (storage & FGFRFT_STORE_C64) ? (float2*)(pm + lay.off_c64) : nullptr;
+  p->f16 = (storage & FGFRFT_STORE_SPLIT_F16) ? (__half*)(pm + lay.off_f16) : nullptr;
+
+  const int n = (int)N;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  double2* Am = (double2*)work;
+  double2* Bm = Am + N * N;
+  double2* Cm = Bm + N * N;
+  double* red = (double*)((char*)work + align_up((size_t)3 * N * N * sizeof(double2)));
+  double h[3];
+  auto fail = [&](int code) {
+    free(p);
+    return code;
+  };
+  auto readback = [&](void) -> bool {
+    if (cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+    return cudaStreamSynchronize(s) == cudaSuccess;
+  };
+
+  if (cudaMemsetAsync(plan_mem, 0, kAlign, s) != cudaSuccess) return fail(FGFRFT_ERR_CUDA);
+  // (1) unitarity: ||F^H F - I||_F / sqrt(N)
+  if (fg_zgemm(true, false, n, n, n, one, (const double2*)F_dev, n, (const double2*)F_dev, n, zero, Am, n, s) ||
+      fg_zaxpby_identity(N, zero, nullptr, one, make_double2(-1.0, 0.0), Am, s) ||
+      fg_ztrace_fro(N, Am, nullptr, red, s) || !readback())
+    return fail(FGFRFT_ERR_CUDA);
+  if (!(sqrt(h[1]) / sqrt((double)N) <= 1e-8)) return fail(FGFRFT_ERR_NOT_UNITARY);
+
+  // (2) projector P onto the lambda = -1 eigenspace, into Cm
+  int squarings = 0;
+  if (W_dev) {
+    if (r_W > 0) {
+      if (fg_zgemm(false, true, n, n, (int)r_W, one, (const double2*)W_dev, (int)r_W, (const double2*)W_dev,
+                   (int)r_W, zero, Cm, n, s))
+        return fail(FGFRFT_ERR_CUDA);
+    } else if (cudaMemsetAsync(Cm, 0, (size_t)N * N * sizeof(double2), s) != cudaSuccess) {
+      return fail(FGFRFT_ERR_CUDA);
+    }
+  } else {
+    // T = (I - F)/2 -> Am;  S = T T^H -> Bm  (eigenvalues sin^2(theta_k/2))
+    if (fg_zaxpby_identity(N, make_double2(-0.5, 0.0), (const double2*)F_dev, zero, make_double2(0.5, 0.0), Am, s) ||
+        fg_zgemm(false, true, n, n, n, one, Am, n, Am, n, zero, Bm, n, s))
+      return fail(FGFRFT_ERR_CUDA);
+    double2* cur = Bm;
+    double2* tmp = Am;
+    bool converged = false;
+    // Square until every eigenvalue is within the basin of McWeeny purification:
+    // tr(S) - ||S||_F^2 = sum s_k (1 - s_k) < 0.05 puts each s_k below 0.053 or above 0.947.
+    for (squarings = 1; squarings <= 46; ++squarings) {
+      if (fg_zgemm(false, false, n, n, n, one, cur, n, cur, n, zero, tmp, n, s) || fg_zherm_sym(N, tmp, s))
+        return fail(FGFRFT_ERR_CUDA);
+      std::swap(cur, tmp);
+      if (fg_ztrace_fro(N, cur, nullptr, red, s) || !readback()) return fail(FGFRFT_ERR_CUDA);
+      if (h[0] - h[1] < 0.05) {
+        converged = true;
+        break;
+      }
+    }
+    if (!converged) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
+    // McWeeny purification P <- 3 P^2 - 2 P^3 (quadratic convergence to 0 / 1)
+    for (int it = 0; it < 12; ++it) {
+      if (fg_zgemm(false, false, n, n, n, one, cur, n, cur, n, zero, tmp, n, s) ||  // P^2
+          fg_zgemm(false, false, n, n, n, one, tmp, n, cur, n, zero, Cm, n, s) ||   // P^3
+          fg_ztrace_fro(N, tmp, cur, red, s) || !readback())                         // ||P^2 - P||
+        return fail(FGFRFT_ERR_CUDA);
+      if (fg_zmcweeny(N, tmp, Cm, cur, s) || fg_zherm_sym(N, cur, s)) return fail(FGFRFT_ERR_CUDA);
+      if (sqrt(h[1]) < 1e-13 * sqrt((double)N)) break;
+    }
+    if (cudaMemcpyAsync(Cm, cur, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail(FGFRFT_ERR_CUDA);
+  }
+  if (fg_ztrace_fro(N, Cm, nullptr, red, s) || !readback()) return fail(FGFRFT_ERR_CUDA);
+  p->r_neg1 = (int)llround(h[0]);
+  if (p->r_neg1 < 0 || fabs(h[0] - p->r_neg1) > 1e-6) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
+  if (p->r_neg1 == 0 && cudaMemsetAsync(Cm, 0, (size_t)N * N * sizeof(double2), s) != cudaSuccess)
+    return fail(FGFRFT_ERR_CUDA);
+  p->squarings = squarings;
+  // residual ||F P + P||_F
+  if (fg_zgemm(false, false, n, n, n, one, (const double2*)F_dev, n, Cm, n, zero, Am, n, s) ||
+      fg_zaxpby_identity(N, one, Cm, one, zero, Am, s) || fg_ztrace_fro(N, Am, nullptr, red, s) || !readback())
+    return fail(FGFRFT_ERR_CUDA);
+  p->proj_residual = sqrt(h[1]);
+  if (p->r_neg1 > 0 && !(p->proj_residual <= 1e-6 * sqrt((double)p->r_neg1))) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
+
+  // (3) powers: M_0 = P_c = I - P, M_n = F M_{n-1}; M_{-n} = M_n^H.  Round into storage.
+  auto store = [&](int blk, const double2* M, bool conjT) -> bool {
+    float2* c = p->c64 ? p->c64 + (int64_t)blk * p->blk_elems : nullptr;
+    __half* f = p->f16 ? p->f16 + (int64_t)blk * 4 * p->plane_elems : nullptr;
+    return fg_store_block(N, M, conjT, c, f, p->Np, p->plane_elems, s) == cudaSuccess;
+  };
+  if (!store(blk_of_P(p), Cm, false)) return fail(FGFRFT_ERR_CUDA);
+  if (fg_zaxpby_identity(N, make_double2(-1.0, 0.0), Cm, zero, one, Am, s)) return fail(FGFRFT_ERR_CUDA);
+  if (!store(blk_of_power(p, 0), Am, false)) return fail(FGFRFT_ERR_CUDA);
+  double2* cur = Am;
+  double2* nxt = Bm;
+  for (int k = 1; k <= L_max; ++k) {
+    if (fg_zgemm(false, false, n, n, n, one, (const double2*)F_dev, n, cur, n, zero, nxt, n, s))
+      return fail(FGFRFT_ERR_CUDA);
+    if (!store(blk_of_power(p, k), nxt, false) || !store(blk_of_power(p, -k), nxt, true)) return fail(FGFRFT_ERR_CUDA);
+    std::swap(cur, nxt);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FGFRFT_ERR_CUDA);
+  *out = p;
+  return FGFRFT_OK;
+}
+
+int fgfrft_plan_info(fgfrft_plan p, int64_t* N, int* L_max, int* storage, int* r_neg1, double* proj_residual,
+                     int* squarings, size_t* plan_bytes) {
+  if (!p) return FGFRFT_ERR_INVALID_ARG;
+  if (N) *N = p->N;
+  if (L_max) *L_max = p->L_max;
+  if (storage) *storage = p->storage;
+  if (r_neg1) *r_neg1 = p->r_neg1;
+  if (proj_residual) *proj_residual = p->proj_residual;
+  if (squarings) *squarings = p->squarings;
+  if (plan_bytes) *plan_bytes = p->bytes;
+  return FGFRFT_OK;
+}
+
+const void* fgfrft_plan_block(fgfrft_plan p, int storage, int l, int64_t* block_stride_elems) {
+  if (!p || l < -p->L_max || l > p->L_max + 1) return nullptr;
+  const int blk = l == p->L_max + 1 ? blk_of_P(p) : blk_of_power(p, l);
+  if (storage == FGFRFT_STORE_C64 && p->c64) {
+    if (block_stride_elems) *block_stride_elems = p->blk_elems;
+    return p->c64 + (int64_t)blk * p->blk_elems;
+  }
+  if (storage == FGFRFT_STORE_SPLIT_F16 && p->f16) {
+    if (block_stride_elems) *block_stride_elems = 4 * p->plane_elems;
+    return p->f16 + (int64_t)blk * 4 * p->plane_elems;
+  }
+  return nullptr;
+}
+
+int fgfrft_plan_status(fgfrft_plan p, void* stream) {
+  if (!p) return FGFRFT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t w = 0;
+  CK(cudaMemcpyAsync(&w, p->dstatus, sizeof(w), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (w) {
+    CK(cudaMemsetAsync(p->dstatus, 0, sizeof(w), s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (w & FG_STATUS_WAIT_TIMEOUT) return FGFRFT_ERR_TIMEOUT;
+  return FGFRFT_OK;
+}
+
+int fgfrft_plan_destroy(fgfrft_plan p) {
+  if (!p) return FGFRFT_ERR_INVALID_ARG;
+  free(p);
+  return FGFRFT_OK;
+}
+
+size_t fgfrft_work_bytes(fgfrft_plan p, int op, const double* alpha_host, int64_t count, int L, int flags) {
+  if (!p || count < 1 || L < 0 || L > p->L_max) return 0;
+  std::vector<double> a;
+  if (op == FGFRFT_OP_ASSEMBLE) {
+    if (!alpha_host) return 0;
+    return align_up((size_t)count * sizeof(double)) + align_up((size_t)(2 * L + 2) * count * sizeof(float2));
+  }
+  if (gather_orders(alpha_host, count, L, flags, a) != FGFRFT_OK) return 0;
+  if (flags & FGFRFT_ADJOINT)
+    for (auto& v : a) v = -v;
+  int path = op == FGFRFT_OP_GRAD ? ((flags & FGFRFT_PATH_MASK) ? (flags & FGFRFT_PATH_MASK)
+                                                                 : ((p->storage & FGFRFT_STORE_SPLIT_F16) &&
+                                                                            fg_tc_available()
+                                                                        ? FGFRFT_PATH_STACKED
+                                                                        : FGFRFT_PATH_STACKED_FP32))
+                                  : choose_path(p, a, flags);
+  const int64_t groups = (int64_t)order_runs(a).size();
+  return carve_apply(p, nullptr, count, L, path, groups, op == FGFRFT_OP_GRAD).bytes;
+}
+
+int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, void* Q_dev, void* work,
+                    size_t work_bytes, void* stream) {
+  if (!p || !alpha_host || A < 1 || !Q_dev || !work || L < 0) return FGFRFT_ERR_INVALID_ARG;
+  if (L > p->L_max || !p->c64) return FGFRFT_ERR_UNSUPPORTED;
+  if (A > 65535) return FGFRFT_ERR_INVALID_ARG;
+  std::vector<double> a;
+  int rc = gather_orders(alpha_host, A, L, 0, a);
+  if (rc) return rc;
+  if (work_bytes < fgfrft_work_bytes(p, FGFRFT_OP_ASSEMBLE, alpha_host, A, L, 0) || !aligned(work) ||
+      !aligned(Q_dev, 16))
+    return FGFRFT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Carve c{(char*)work};
+  double* alpha_dev = c.take<double>((size_t)A);
+  float2* coef = c.take<float2>((size_t)(2 * L + 2) * A);
+  CK(cudaMemcpyAsync(alpha_dev, a.data(), (size_t)A * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(fg_coeffs(alpha_dev, (int)A, L, false, coef, nullptr, A, 1, s));
+  const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
+  if (A == 1)
+    CK(fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, coef, (float2*)Q_dev, p->dstatus, s));
+  else
+    CK(fg_assemble_multi(p->c64, p->blk_elems, b0, nb, pb, p->N, (int)A, coef, (float2*)Q_dev, nullptr, p->Np,
+                         p->plane_elems, p->dstatus, s));
+  return FGFRFT_OK;
+}
+
+static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, const void* X_dev, void* Y_dev,
+                      void* D_dev, int path, void* work, size_t work_bytes, cudaStream_t s) {
+  const auto runs = order_runs(a);
+  const int64_t groups = (int64_t)runs.size();
+  ApplyWork w = carve_apply(p, (char*)work, B, L, path, groups, false);
+  if (work_bytes < w.bytes) return FGFRFT_ERR_INVALID_ARG;
+  const int n = (int)p->N;
+  const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
+  const float2* X = (const float2*)X_dev;
+  float2* Y = (float2*)Y_dev;
+  switch (path) {
+    case FGFRFT_PATH_PLAIN: {
+      if (!p->c64) return FGFRFT_ERR_UNSUPPORTED;
+      std::vector<double> ga((size_t)groups);
+      for (int64_t g = 0; g < groups; ++g) ga[(size_t)g] = a[(size_t)runs[(size_t)g].first];
+      CK(cudaMemcpyAsync(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      // coefficient vectors one per order, contiguous: [groups][2L+2]
+      CK(fg_coeffs(w.group_alpha_dev, (int)groups, L, false, w.coef, nullptr, 1, nb + 1, s));
+      for (int64_t g = 0; g < groups; ++g) {
+        // per order: stream the stack once into Q (K1), then Q X on FP32 CUDA cores
+        CK(fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, w.coef + g * (nb + 1), w.Qc,
+                              p->dstatus, s));
+        SimtStackArgs sa{};
+        sa.A = w.Qc;
+        sa.blk_elems = 0;
+        sa.lda = n;
+        sa.b0 = 0;
+        sa.nb_pow = 1;
+        sa.p_blk = -1;
+        sa.N = n;
+        sa.ncols = (int)runs[(size_t)g].second;
+        sa.X = X + runs[(size_t)g].first * p->N;
+        sa.Y = Y + runs[(size_t)g].first * p->N;
+        CK(fg_simt_stacked(sa, s));
+      }
+      return FGFRFT_OK;
+    }
+    case FGFRFT_PATH_STACKED_FP32: {
+      if (!p->c64) return FGFRFT_ERR_UNSUPPORTED;
+      CK(cudaMemcpyAsync(w.alpha_dev, a.data(), (size_t)B * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(fg_coeffs(w.alpha_dev, (int)B, L, false, w.coef, D_dev ? w.coefd : nullptr, B, 1, s));
+      SimtStackArgs sa{};
+      sa.A = p->c64;
+      sa.blk_elems = p->blk_elems;
+      sa.lda = n;
+      sa.b0 = b0;
+      sa.nb_pow = nb;
+      sa.p_blk = pb;
+      sa.N = n;
+      sa.X = X;
+      sa.ldcoef = (int)B;
+      for (int64_t j0 = 0; j0 < B; j0 += 65535LL * 64) {
+        const int64_t nc = std::min<int64_t>(B - j0, 65535LL * 64);
+        sa.ncols = (int)nc;
+        sa.X = X + j0 * p->N;
+        sa.Y = Y ? Y + j0 * p->N : nullptr;
+        sa.D = D_dev ? (float2*)D_dev + j0 * p->N : nullptr;
+        sa.coef = w.coef + j0;
+        sa.coefd = w.coefd + j0;
+        CK(fg_simt_stacked(sa, s));
+      }
+      return FGFRFT_OK;
+    }
+    case FGFRFT_PATH_ASSEMBLED: {
+      if (!p->c64 || !fg_tc_available()) return FGFRFT_ERR_UNSUPPORTED;
+      std::vector<double> ga((size_t)groups);
+      std::vector<int64_t> gstart((size_t)groups), gcount((size_t)groups);
+      for (int64_t g = 0; g < groups; ++g) {
+        ga[(size_t)g] = a[(size_t)runs[(size_t)g].first];
+        gstart[(size_t)g] = runs[(size_t)g].first;
+        gcount[(size_t)g] = runs[(size_t)g].second;
+      }
+      CK(cudaMemcpyAsync(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(fg_coeffs(w.group_alpha_dev, (int)groups, L, false, w.coef, nullptr, groups, 1, s));
+      CK(fg_assemble_multi(p->c64, p->blk_elems, b0, nb, pb, p->N, (int)groups, w.coef, nullptr, w.Qs, p->Np,
+                           p->plane_elems, p->dstatus, s));
+      TcGroupedArgs ta{};
+      ta.N = p->N;
+      ta.Np = p->Np;
+      ta.plane_elems = p->plane_elems;
+      ta.Qs = w.Qs;
+      ta.groups = groups;
+      ta.gstart = gstart.data();
+      ta.gcount = gcount.data();
+      ta.X = X;
+      ta.Y = Y;
+      ta.Xs = w.Xs;
+      ta.xs_rows = w.xs_rows;
+      ta.col_exp = w.col_exp;
+      ta.B = B;
+      ta.scratch = w.tc_scratch;
+      ta.scratch_bytes = w.tc_scratch_bytes;
+      ta.status = p->dstatus;
+      CK(fg_tc_grouped_apply(ta, s));
+      return FGFRFT_OK;
+    }
+    case FGFRFT_PATH_STACKED: {
+      if (!p->f16 || !fg_tc_available()) return FGFRFT_ERR_UNSUPPORTED;
+      CK(cudaMemcpyAsync(w.alpha_dev, a.data(), (size_t)B * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(fg_coeffs(w.alpha_dev, (int)B, L, false, w.coef, D_dev ? w.coefd : nullptr, B, 1, s));
+      TcStackedArgs ta{};
+      ta.N = p->N;
+      ta.Np = p->Np;
+      ta.plane_elems = p->plane_elems;
+      ta.stack = p->f16;
+      ta.b0 = b0;
+      ta.nb_pow = nb;
+      ta.p_blk = pb;
+      ta.X = X;
+      ta.Y = Y;
+      ta.D = (float2*)D_dev;
+      ta.coef = w.coef;
+      ta.coefd = w.coefd;
+      ta.B = B;
+      ta.Xs = w.Xs;
+      ta.xs_rows = w.xs_rows;
+      ta.col_exp = w.col_exp;
+      ta.scratch = w.tc_scratch;
+      ta.scratch_bytes = w.tc_scratch_bytes;
+      ta.status = p->dstatus;
+      CK(fg_tc_stacked_apply(ta, s));
+      return FGFRFT_OK;
+    }
+    default:
+      return FGFRFT_ERR_INVALID_ARG;
+  }
+}
+
+int fgfrft_apply(fgfrft_plan p, const double* alpha_host, int64_t B, int L, const void* X_dev, void* Y_dev,
+                 int flags, void* work, size_t work_bytes, void* stream) {
+  if (!p || !alpha_host || B < 1 || !X_dev || !Y_dev || !work || L < 0) return FGFRFT_ERR_INVALID_ARG;
+  if (L > p->L_max) return FGFRFT_ERR_UNSUPPORTED;
+  if (!aligned(work) || !aligned(X_dev, 8) || !aligned(Y_dev, 8)) return FGFRFT_ERR_INVALID_ARG;
+  std::vector<double> a;
+  int rc = gather_orders(alpha_host, B, L, flags, a);
+  if (rc) return rc;
+  if (flags & FGFRFT_ADJOINT)
+    for (auto& v : a) v = -v;
+  const int path = choose_path(p, a, flags);
+  if (path == FGFRFT_PATH_PLAIN && !p->c64) return FGFRFT_ERR_UNSUPPORTED;
+  return apply_impl(p, a, B, L, X_dev, Y_dev, nullptr, path, work, work_bytes, (cudaStream_t)stream);
+}
+
+int fgfrft_grad(fgfrft_plan p, const double* alpha_host, int64_t B, int L, const void* X_dev, void* Y_dev,
+                void* dY_dev, const void* G_dev, void* gradX_dev, float* gradalpha_dev, int flags, void* work,
+                size_t work_bytes, void* stream) {
+  if (!p || !alpha_host || B < 1 || !work || L < 0) return FGFRFT_ERR_INVALID_ARG;
+  if (L > p->L_max) return FGFRFT_ERR_UNSUPPORTED;
+  if (!X_dev && !G_dev) return FGFRFT_ERR_INVALID_ARG;
+  if (X_dev && !Y_dev && !dY_dev) return FGFRFT_ERR_INVALID_ARG;
+  if (G_dev && !gradX_dev && !gradalpha_dev) return FGFRFT_ERR_INVALID_ARG;
+  if (gradalpha_dev && !dY_dev) return FGFRFT_ERR_INVALID_ARG;
+  if (!aligned(work)) return FGFRFT_ERR_INVALID_ARG;
+  std::vector<double> a;
+  int rc = gather_orders(alpha_host, B, L, flags & ~FGFRFT_ADJOINT, a);
+  if (rc) return rc;
+  int path = flags & FGFRFT_PATH_MASK;
+  if (!path)
+    path = (p->f16 && fg_tc_available()) ? FGFRFT_PATH_STACKED : FGFRFT_PATH_STACKED_FP32;
+  if (path != FGFRFT_PATH_STACKED && path != FGFRFT_PATH_STACKED_FP32) return FGFRFT_ERR_UNSUPPORTED;
+  ApplyWork w = carve_apply(p, (char*)work, B, L, path, 1, true);
+  if (work_bytes < w.bytes) return FGFRFT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (X_dev) {
+    rc = apply_impl(p, a, B, L, X_dev, Y_dev, dY_dev, path, work, work_bytes, s);
+    if (rc) return rc;
+  }
+  if (G_dev) {
+    if (gradalpha_dev) CK(fg_grad_alpha((const float2*)G_dev, (const float2*)dY_dev, B, p->N, gradalpha_dev, w.partials, s));
+    if (gradX_dev) {
+      std::vector<double> na(a);
+      for (auto& v : na) v = -v;
+      rc = apply_impl(p, na, B, L, G_dev, gradX_dev, nullptr, path, work, work_bytes, s);
+      if (rc) return rc;
+    }
+  }
+  return FGFRFT_OK;
+}
+
+}  // extern "C"

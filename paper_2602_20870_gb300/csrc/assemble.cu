@@ -1,0 +1,348 @@
+// Online operator assembly (Def. 1; Algorithm 1, online part):
+//   Q = e^{j pi a} P + sum_{l=-L}^{L} c_l(a) M_l
+// is a streaming linear combination of 2L + 2 stored N x N blocks, bound by HBM
+// bandwidth.  Each CTA owns a contiguous chunk of entries and walks the blocks in
+// order; one thread stages (chunk, block) tiles into a shared-memory ring with 1-D
+// bulk copies (cp.async.bulk, completion on an mbarrier), so the loads in flight per
+// SM are bounded by the ring size rather than by registers.
+#include "internal.h"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// K1: one order.  CHUNK complex entries per tile, STAGES ring slots.
+// ---------------------------------------------------------------------------
+constexpr int K1_THREADS = 256;
+constexpr int K1_CHUNK = 2048;                      // 16 KB of c64 per tile
+constexpr int K1_STAGES = 6;                        // 96 KB ring per CTA
+constexpr int K1_PER_THREAD = K1_CHUNK / K1_THREADS;  // 8 entries (4 x float4)
+constexpr int K1_MAXBLK = 1024;
+
+struct K1Smem {
+  float4 ring[K1_STAGES][K1_CHUNK / 2];
+  float2 coef[K1_MAXBLK];
+  uint64_t full[K1_STAGES];
+};
+
+__global__ void __launch_bounds__(K1_THREADS) assemble_single_kernel(const float2* __restrict__ stack,
+                                                                     int64_t blk_elems, int b0, int nb_pow,
+                                                                     int p_blk, int64_t NN,
+                                                                     const float2* __restrict__ coef,
+                                                                     float2* __restrict__ Q, uint32_t* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  K1Smem& sm = *reinterpret_cast<K1Smem*>(smem_raw);
+  const int nblk = nb_pow + (p_blk >= 0 ? 1 : 0);
+  const int tid = threadIdx.x;
+  for (int b = tid; b < nblk; b += K1_THREADS) sm.coef[b] = coef[b];
+  if (tid == 0) {
+    for (int s = 0; s < K1_STAGES; ++s) mbar_init(&sm.full[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  const int64_t ntiles = (NN + K1_CHUNK - 1) / K1_CHUNK;
+  // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t items = my_tiles * nblk;
+  uint64_t policy = 0;
+  if (tid == 0) policy = policy_evict_first();
+
+  auto issue = [&](int64_t item) {
+    const int s = (int)(item % K1_STAGES);
+    const int64_t t = blockIdx.x + (item / nblk) * gridDim.x;
+    const int b = (int)(item % nblk);
+    const int blk = b < nb_pow ? b0 + b : p_blk;
+    const int64_t e0 = t * K1_CHUNK;
+    const int64_t cnt = (NN - e0) < K1_CHUNK ? (NN - e0) : K1_CHUNK;
+    // byte count rounded up to 16: the block stride is padded to 32 entries, so
+    // the over-read stays inside the block's padding.
+    const uint32_t bytes = (uint32_t)(((cnt * 8) + 15) & ~int64_t(15));
+    mbar_arrive_expect_tx(&sm.full[s], bytes);
+    bulk_g2s_evict_first(&sm.ring[s][0], stack + (int64_t)blk * blk_elems + e0, bytes, &sm.full[s], policy);
+  };
+
+  if (tid == 0) {
+    const int64_t pre = items < K1_STAGES ? items : K1_STAGES;
+    for (int64_t it = 0; it < pre; ++it) issue(it);
+  }
+
+  float2 acc[K1_PER_THREAD];
+#pragma unroll
+  for (int e = 0; e < K1_PER_THREAD; ++e) acc[e] = make_float2(0.f, 0.f);
+
+  bool ok = true;
+  for (int64_t it = 0; it < items; ++it) {
+    const int s = (int)(it % K1_STAGES);
+    const uint32_t parity = (uint32_t)((it / K1_STAGES) & 1);
+    const int b = (int)(it % nblk);
+    if (ok) ok = mbar_wait(&sm.full[s], parity, status);
+    const float2 c = sm.coef[b];
+    if (ok) {
+#pragma unroll
+      for (int v = 0; v < K1_PER_THREAD / 2; ++v) {
+        const float4 x = sm.ring[s][tid + v * K1_THREADS];
+        // entries 2*(tid + v*256) and +1
+        acc[2 * v].x = fmaf(c.x, x.x, fmaf(-c.y, x.y, acc[2 * v].x));
+        acc[2 * v].y = fmaf(c.x, x.y, fmaf(c.y, x.x, acc[2 * v].y));
+        acc[2 * v + 1].x = fmaf(c.x, x.z, fmaf(-c.y, x.w, acc[2 * v + 1].x));
+        acc[2 * v + 1].y = fmaf(c.x, x.w, fmaf(c.y, x.z, acc[2 * v + 1].y));
+      }
+    }
+    __syncthreads();  // every thread is done with slot s
+    if (tid == 0 && ok && it + K1_STAGES < items) issue(it + K1_STAGES);
+    if (b == nblk - 1) {
+      const int64_t t = blockIdx.x + (it / nblk) * gridDim.x;
+      const int64_t e0 = t * K1_CHUNK;
+#pragma unroll
+      for (int v = 0; v < K1_PER_THREAD / 2; ++v) {
+        const int64_t e = e0 + 2 * (tid + (int64_t)v * K1_THREADS);
+        if (e < NN) Q[e] = acc[2 * v];
+        if (e + 1 < NN) Q[e + 1] = acc[2 * v + 1];
+        acc[2 * v] = make_float2(0.f, 0.f);
+        acc[2 * v + 1] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  // drain: if a wait failed, the copies already issued may still land; wait for
+  // each outstanding slot (bounded) before the CTA's shared memory is released.
+  if (!ok && tid == 0) {
+    for (int s = 0; s < K1_STAGES; ++s) {
+      const uint64_t t0 = global_timer_ns();
+      while (!mbar_try_wait(&sm.full[s], 0) && !mbar_try_wait(&sm.full[s], 1)) {
+        if (global_timer_ns() - t0 > FG_WAIT_LIMIT_NS) break;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: A orders in one pass.  Each thread owns EPT complex entries and AC order
+// accumulators per entry; the real coefficients of the powers [nb_pow][AC] and
+// the complex coefficients of P [AC] live in shared memory (broadcast reads).
+// ---------------------------------------------------------------------------
+constexpr int K2_THREADS = 256;
+constexpr int K2_STAGES = 8;
+
+template <int AC, int EPT, bool SPLIT>
+__global__ void __launch_bounds__(K2_THREADS) assemble_multi_kernel(
+    const float2* __restrict__ stack, int64_t blk_elems, int b0, int nb_pow, int p_blk, int64_t N, int A, int a0,
+    const float2* __restrict__ coef, float2* __restrict__ Qc, __half* __restrict__ Qs, int64_t Np,
+    int64_t plane_elems, uint32_t* status) {
+  constexpr int CHUNK = K2_THREADS * EPT;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* ring = reinterpret_cast<float2*>(smem_raw);            // [STAGES][CHUNK]
+  float2* cpx = ring + K2_STAGES * CHUNK;                        // [AC] complex coefficients of P
+  float* cre = reinterpret_cast<float*>(cpx + AC);               // [nb_pow][AC] real coefficients
+  uint64_t* full = reinterpret_cast<uint64_t*>(cre + (size_t)nb_pow * AC + ((nb_pow * AC) & 1));
+  const bool has_p = p_blk >= 0;
+  const int nblk = nb_pow + (has_p ? 1 : 0);
+  const int tid = threadIdx.x;
+  const int na = (A - a0) < AC ? (A - a0) : AC;
+  for (int t = tid; t < nb_pow * AC; t += K2_THREADS) {
+    const int b = t / AC, a = t % AC;
+    cre[t] = a < na ? coef[(size_t)b * A + a0 + a].x : 0.f;
+  }
+  for (int a = tid; a < AC; a += K2_THREADS)
+    cpx[a] = (has_p && a < na) ? coef[(size_t)nb_pow * A + a0 + a] : make_float2(0.f, 0.f);
+  if (tid == 0) {
+    for (int s = 0; s < K2_STAGES; ++s) mbar_init(&full[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const int64_t NN = N * N;
+  const int64_t ntiles = (NN + CHUNK - 1) / CHUNK;
+  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t items = my_tiles * nblk;
+  auto issue = [&](int64_t item) {
+    const int s = (int)(item % K2_STAGES);
+    const int64_t t = blockIdx.x + (item / nblk) * gridDim.x;
+    const int b = (int)(item % nblk);
+    const int blk = b < nb_pow ? b0 + b : p_blk;
+    const int64_t e0 = t * CHUNK;
+    const int64_t cnt = (NN - e0) < CHUNK ? (NN - e0) : CHUNK;
+    const uint32_t bytes = (uint32_t)(((cnt * 8) + 15) & ~int64_t(15));
+    mbar_arrive_expect_tx(&full[s], bytes);
+    bulk_g2s(ring + (size_t)s * CHUNK, stack + (int64_t)blk * blk_elems + e0, bytes, &full[s]);
+  };
+  if (tid == 0) {
+    const int64_t pre = items < K2_STAGES ? items : K2_STAGES;
+    for (int64_t it = 0; it < pre; ++it) issue(it);
+  }
+  float2 acc[EPT][AC];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e)
+#pragma unroll
+    for (int a = 0; a < AC; ++a) acc[e][a] = make_float2(0.f, 0.f);
+  bool ok = true;
+  for (int64_t it = 0; it < items; ++it) {
+    const int s = (int)(it % K2_STAGES);
+    const uint32_t parity = (uint32_t)((it / K2_STAGES) & 1);
+    const int b = (int)(it % nblk);
+    if (ok) ok = mbar_wait(&full[s], parity, status);
+    if (ok) {
+      float2 x[EPT];
+      if (EPT == 2) {
+        const float4 v = reinterpret_cast<const float4*>(ring + (size_t)s * CHUNK)[tid];
+        x[0] = make_float2(v.x, v.y);
+        x[EPT - 1] = make_float2(v.z, v.w);
+      } else {
+        x[0] = ring[(size_t)s * CHUNK + tid];
+      }
+      if (b < nb_pow) {  // real coefficient: 2 FMAs per entry and order
+        const float4* cb = reinterpret_cast<const float4*>(cre + (size_t)b * AC);
+#pragma unroll
+        for (int a4 = 0; a4 < AC / 4; ++a4) {
+          const float4 c = cb[a4];
+          const float cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+              acc[e][4 * a4 + q].x = fmaf(cc[q], x[e].x, acc[e][4 * a4 + q].x);
+              acc[e][4 * a4 + q].y = fmaf(cc[q], x[e].y, acc[e][4 * a4 + q].y);
+            }
+        }
+      } else {  // the P block: complex coefficient e^{j pi a} (or its derivative)
+#pragma unroll
+        for (int a = 0; a < AC; ++a) {
+          const float2 c = cpx[a];
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) cmac(acc[e][a], c, x[e]);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && ok && it + K2_STAGES < items) issue(it + K2_STAGES);
+    if (b == nblk - 1) {
+      const int64_t t = blockIdx.x + (it / nblk) * gridDim.x;
+      const int64_t e = t * CHUNK + (int64_t)EPT * tid;
+#pragma unroll
+      for (int ee = 0; ee < EPT; ++ee) {
+        const int64_t g = e + ee;
+        if (g < NN) {
+          const int64_t i = g / N, k = g % N;
+#pragma unroll
+          for (int a = 0; a < AC; ++a) {
+            if (a < na) {
+              const float2 v = acc[ee][a];
+              if (!SPLIT) {
+                Qc[(int64_t)(a0 + a) * NN + g] = v;
+              } else {
+                const float sc = (float)(1 << FG_SPLIT_SHIFT);
+                const float re = v.x * sc, im = v.y * sc;
+                const __half rh = __float2half_rn(re), ih = __float2half_rn(im);
+                const __half rl = __float2half_rn(re - __half2float(rh));
+                const __half il = __float2half_rn(im - __half2float(ih));
+                __half* base = Qs + (int64_t)(a0 + a) * 4 * plane_elems + i * Np + k;
+                base[0] = rh;
+                base[plane_elems] = rl;
+                base[2 * plane_elems] = ih;
+                base[3 * plane_elems] = il;
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < AC; ++a) acc[ee][a] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  if (!ok && tid == 0) {
+    for (int s = 0; s < K2_STAGES; ++s) {
+      const uint64_t t0 = global_timer_ns();
+      while (!mbar_try_wait(&full[s], 0) && !mbar_try_wait(&full[s], 1)) {
+        if (global_timer_ns() - t0 > FG_WAIT_LIMIT_NS) break;
+      }
+    }
+  }
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int AC, bool SPLIT>
+cudaError_t launch_multi(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk, int64_t N, int A,
+                         int a0, const float2* coef, float2* Qc, __half* Qs, int64_t Np, int64_t plane_elems,
+                         uint32_t* status, cudaStream_t s) {
+  constexpr int EPT = AC >= 64 ? 1 : 2;
+  constexpr int CHUNK = K2_THREADS * EPT;
+  const size_t smem = (size_t)K2_STAGES * CHUNK * sizeof(float2) + AC * sizeof(float2) +
+                      ((size_t)nb_pow * AC + 1) * sizeof(float) + K2_STAGES * sizeof(uint64_t) + 16;
+  auto kern = assemble_multi_kernel<AC, EPT, SPLIT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t NN = N * N;
+  const int64_t ntiles = (NN + CHUNK - 1) / CHUNK;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K2_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms() * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  kern<<<(unsigned)grid, K2_THREADS, smem, s>>>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
+                                                plane_elems, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t fg_assemble_single(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk, int64_t NN,
+                               const float2* coef, float2* Q, uint32_t* status, cudaStream_t s) {
+  const int nblk = nb_pow + (p_blk >= 0 ? 1 : 0);
+  if (nblk > K1_MAXBLK) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(K1Smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(assemble_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assemble_single_kernel, K1_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t ntiles = (NN + K1_CHUNK - 1) / K1_CHUNK;
+  int64_t grid = (int64_t)num_sms() * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  assemble_single_kernel<<<(unsigned)grid, K1_THREADS, smem, s>>>(stack, blk_elems, b0, nb_pow, p_blk, NN, coef, Q,
+                                                                   status);
+  return cudaGetLastError();
+}
+
+cudaError_t fg_assemble_multi(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk, int64_t N,
+                              int A, const float2* coef, float2* Qc, __half* Qs, int64_t Np, int64_t plane_elems,
+                              uint32_t* status, cudaStream_t s) {
+  // orders in passes of at most 64 (one pass over the stack per 64 orders)
+  for (int a0 = 0; a0 < A; a0 += 64) {
+    const int na = (A - a0) < 64 ? (A - a0) : 64;
+    cudaError_t e;
+    const bool split = Qs != nullptr;
+    if (na <= 8)
+      e = split ? launch_multi<8, true>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np, plane_elems,
+                                        status, s)
+                : launch_multi<8, false>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
+                                         plane_elems, status, s);
+    else if (na <= 16)
+      e = split ? launch_multi<16, true>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
+                                         plane_elems, status, s)
+                : launch_multi<16, false>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
+                                          plane_elems, status, s);
+    else if (na <= 32)
+      e = split ? launch_multi<32, true>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
+                                         plane_elems, status, s)
+                : launch_multi<32, false>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
+                                          plane_elems, status, s);
+    else
+      e = split ? launch_multi<64, true>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
+                                         plane_elems, status, s)
+                : launch_multi<64, false>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
+                                          plane_elems, status, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}

@@ -1,0 +1,494 @@
+// Tensor-core (tcgen05) complex GEMM over stacked blocks, split-fp16 operands.
+//
+//   T_b = A_b[rows, :] X[cols, :]^T            (complex, K = N; Def. 2 x~ = Q x)
+//   Y[j] (+)= coef[b][j] T_b[:, j]              (Def. 1 per column; or Y = T when
+//   D[j] (+)= coefd[b][j] T_b[:, j]              there is one block per tile, Prop. 3)
+//
+// Operands are stored as four fp16 planes {re_hi, re_lo, im_hi, im_lo}: A scaled by
+// 2^FG_SPLIT_SHIFT, signal column j by 2^{e_j}; hi = fp16(v), lo = fp16(v - hi).
+// Each complex product keeps the three significant split products
+// (hi*hi + hi*lo + lo*hi), so every K=16 step issues 12 MMAs:
+//   acc_re += Ar*Xr - Ai*Xi ,  acc_im += Ar*Xi + Ai*Xr   (3 split products each term)
+// with FP32 accumulation in tensor memory (TMEM).
+//
+// CTA layout (192 threads, one CTA per SM, persistent over a tile list):
+//   warp 0      TMA producer: 3-D tensor-map loads of 4 A planes + 4 X planes per
+//               stage (32 k-values, 64-byte swizzled rows) into a 3-stage ring;
+//   warp 1      allocates 512 TMEM columns; one thread issues tcgen05.mma and
+//               tcgen05.commit; accumulators double-buffered (2 x [re 128 | im 128]);
+//   warps 2..5  epilogue: tcgen05.ld the finished block, undo the power-of-two
+//               scales, apply the per-column coefficients, and accumulate into Y/D in
+//               global memory (each output tile is owned by one CTA, blocks in order,
+//               so the sums are deterministic).
+// Every mbarrier wait is bounded; on a timeout the CTA records it in the status word,
+// stops issuing work, waits (bounded) for its copies and MMAs in flight, frees TMEM and
+// returns.
+#include <cuda.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "tc.h"
+
+namespace {
+
+constexpr int TC_BM = 128;                 // rows per tile (TMEM lanes)
+constexpr int TC_BN = 128;                 // complex columns per tile
+constexpr int TC_KC = 32;                  // k per stage: 32 fp16 = 64-byte rows
+constexpr int TC_STAGES = 3;
+constexpr int TC_PLANE_A = TC_BM * TC_KC * 2;  // 8 KB
+constexpr int TC_PLANE_B = TC_BN * TC_KC * 2;  // 8 KB
+constexpr int TC_STAGE_BYTES = 4 * TC_PLANE_A + 4 * TC_PLANE_B;
+constexpr int TC_TMEM_COLS = 512;
+constexpr int TC_THREADS = 192;
+constexpr int TC_EPI_WARP0 = 2;
+
+struct __align__(1024) TcSmem {
+  uint8_t stage[TC_STAGES][TC_STAGE_BYTES];
+  uint64_t full[TC_STAGES];
+  uint64_t empty[TC_STAGES];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  volatile int abort;
+  float scale[TC_BN];
+};
+
+// kind::f16 instruction descriptor: D f32, A/B f16, both K-major, N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+constexpr uint32_t kIdescNegA = kIdesc | (1u << 13);
+
+struct TcParams {
+  const int4* tiles;  // {row tile, A plane base (grouped), first column, end column}
+  int ntiles;
+  int nblk;           // blocks per tile
+  int grouped;        // 1: A plane base from the tile, one block; 0: stacked blocks
+  int b0, nb_pow, p_blk;
+  int N;
+  int kchunks;
+  const float2* coef;
+  const float2* coefd;
+  int64_t ldcoef;
+  float2* Y;
+  float2* D;
+  const int* col_exp;
+  uint32_t* status;
+};
+
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;            // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)4 << 61;                     // 64-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Bounded wait that also gives up at once when another role already aborted.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, TcSmem& sm, uint32_t* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (sm.abort) return false;
+    if (global_timer_ns() - t0 > FG_WAIT_LIMIT_NS) {
+      sm.abort = 1;
+      atomicOr(status, FG_STATUS_WAIT_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  TcSmem& sm = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm.tfull[b], 1);
+      mbar_init(&sm.tempty[b], 4);
+    }
+    mbar_init(&sm.drain, 1);
+    sm.abort = 0;
+    fence_barrier_init();
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_tc_before();
+  __syncthreads();
+  fence_tc_after();
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t kit = 0;
+      uint32_t issued[TC_STAGES] = {0, 0, 0};
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
+        const int4 tile = p.tiles[t];
+        for (int b = 0; ok && b < p.nblk; ++b) {
+          const int zA = p.grouped ? tile.y : 4 * (b < p.nb_pow ? p.b0 + b : p.p_blk);
+          for (int kc = 0; kc < p.kchunks; ++kc, ++kit) {
+            const int s = (int)(kit % TC_STAGES);
+            const uint32_t ph = (kit / TC_STAGES) & 1;
+            if (!tc_wait(&sm.empty[s], ph ^ 1, sm, p.status)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&sm.full[s], TC_STAGE_BYTES);
+            issued[s]++;
+            uint8_t* st = sm.stage[s];
+            const int k0 = kc * TC_KC;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tma_load_3d(st + q * TC_PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              tma_load_3d(st + 4 * TC_PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
+          }
+        }
+      }
+      if (!ok) {  // wait (bounded) until every issued copy has landed
+        for (int s = 0; s < TC_STAGES; ++s) {
+          if (!issued[s]) continue;
+          const uint32_t par = (issued[s] - 1) & 1;
+          const uint64_t t0 = global_timer_ns();
+          while (!mbar_try_wait(&sm.full[s], par) && global_timer_ns() - t0 < FG_WAIT_LIMIT_NS) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t kit = 0, bc = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
+        for (int b = 0; ok && b < p.nblk; ++b, ++bc) {
+          const uint32_t buf = bc & 1, tph = (bc >> 1) & 1;
+          if (!tc_wait(&sm.tempty[buf], tph ^ 1, sm, p.status)) {
+            ok = false;
+            break;
+          }
+          fence_tc_after();
+          const uint32_t d_re = tmem + buf * (2 * TC_BN);
+          const uint32_t d_im = d_re + TC_BN;
+          for (int kc = 0; kc < p.kchunks; ++kc, ++kit) {
+            const int s = (int)(kit % TC_STAGES);
+            const uint32_t ph = (kit / TC_STAGES) & 1;
+            if (!tc_wait(&sm.full[s], ph, sm, p.status)) {
+              ok = false;
+              break;
+            }
+            fence_tc_after();
+            const uint32_t sa = smem_u32(sm.stage[s]);
+            const uint32_t sb = sa + 4 * TC_PLANE_A;
+#pragma unroll
+            for (int kk = 0; kk < TC_KC / 16; ++kk) {
+              const uint32_t off = kk * 32;  // 16 fp16 along k
+              const uint64_t arh = desc_sw64(sa + 0 * TC_PLANE_A + off), arl = desc_sw64(sa + 1 * TC_PLANE_A + off);
+              const uint64_t aih = desc_sw64(sa + 2 * TC_PLANE_A + off), ail = desc_sw64(sa + 3 * TC_PLANE_A + off);
+              const uint64_t brh = desc_sw64(sb + 0 * TC_PLANE_B + off), brl = desc_sw64(sb + 1 * TC_PLANE_B + off);
+              const uint64_t bih = desc_sw64(sb + 2 * TC_PLANE_B + off), bil = desc_sw64(sb + 3 * TC_PLANE_B + off);
+              const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+              // real part: Ar*Xr - Ai*Xi
+              umma(d_re, arh, brh, kIdesc, acc);
+              umma(d_re, arh, brl, kIdesc, 1);
+              umma(d_re, arl, brh, kIdesc, 1);
+              umma(d_re, aih, bih, kIdescNegA, 1);
+              umma(d_re, aih, bil, kIdescNegA, 1);
+              umma(d_re, ail, bih, kIdescNegA, 1);
+              // imaginary part: Ar*Xi + Ai*Xr
+              umma(d_im, arh, bih, kIdesc, acc);
+              umma(d_im, arh, bil, kIdesc, 1);
+              umma(d_im, arl, bih, kIdesc, 1);
+              umma(d_im, aih, brh, kIdesc, 1);
+              umma(d_im, aih, brl, kIdesc, 1);
+              umma(d_im, ail, brh, kIdesc, 1);
+            }
+            umma_commit(&sm.empty[s]);  // stage s is free once these MMAs complete
+          }
+          if (!ok) break;
+          umma_commit(&sm.tfull[buf]);  // block done: accumulators ready for the epilogue
+        }
+      }
+      // wait (bounded) for every MMA this thread issued before TMEM is released
+      umma_commit(&sm.drain);
+      const uint64_t t0 = global_timer_ns();
+      while (!mbar_try_wait(&sm.drain, 0) && global_timer_ns() - t0 < FG_WAIT_LIMIT_NS) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const int row = 32 * q + lane;
+    const int et = threadIdx.x - TC_EPI_WARP0 * 32;  // 0..127
+    uint32_t bc = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
+      const int4 tile = p.tiles[t];
+      epi_bar();
+      {
+        const int j = tile.z + et;
+        const int e = j < tile.w ? p.col_exp[j] : 0;
+        sm.scale[et] = ldexpf(1.0f, -(FG_SPLIT_SHIFT + e));
+      }
+      epi_bar();
+      const int gi = tile.x * TC_BM + row;
+      const bool row_ok = gi < p.N;
+      for (int b = 0; b < p.nblk; ++b, ++bc) {
+        const uint32_t buf = bc & 1, tph = (bc >> 1) & 1;
+        if (!tc_wait(&sm.tfull[buf], tph, sm, p.status)) {
+          ok = false;
+          break;
+        }
+        fence_tc_after();
+        const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + buf * (2 * TC_BN);
+#pragma unroll 1
+        for (int cc = 0; cc < TC_BN / 32; ++cc) {
+          uint32_t vr[32], vi[32];
+          tmem_ld32(base + cc * 32, vr);
+          tmem_ld32(base + TC_BN + cc * 32, vi);
+          tmem_wait_ld();
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            const int jj = cc * 32 + c;
+            const int j = tile.z + jj;
+            if (j < tile.w && row_ok) {
+              const float sc = sm.scale[jj];
+              const float tr = __uint_as_float(vr[c]) * sc, ti = __uint_as_float(vi[c]) * sc;
+              float2* yp = p.Y + (int64_t)j * p.N + gi;
+              if (p.coef == nullptr) {
+                *yp = make_float2(tr, ti);
+              } else {
+                const float2 cf = __ldg(p.coef + (int64_t)b * p.ldcoef + j);
+                float2 y = b == 0 ? make_float2(0.f, 0.f) : *yp;
+                y.x = fmaf(cf.x, tr, fmaf(-cf.y, ti, y.x));
+                y.y = fmaf(cf.x, ti, fmaf(cf.y, tr, y.y));
+                *yp = y;
+                if (p.D) {
+                  const float2 cd = __ldg(p.coefd + (int64_t)b * p.ldcoef + j);
+                  float2* dp = p.D + (int64_t)j * p.N + gi;
+                  float2 d = b == 0 ? make_float2(0.f, 0.f) : *dp;
+                  d.x = fmaf(cd.x, tr, fmaf(-cd.y, ti, d.x));
+                  d.y = fmaf(cd.x, ti, fmaf(cd.y, tr, d.y));
+                  *dp = d;
+                }
+              }
+            }
+          }
+        }
+        fence_tc_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.tempty[buf]);
+      }
+    }
+  }
+  fence_tc_before();
+  __syncthreads();
+  fence_tc_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 3-D fp16 map: dim0 = k (N, contiguous), dim1 = rows (pitch Np), dim2 = planes (stride plane_elems).
+bool make_map(CUtensorMap* m, const void* base, int64_t N, int64_t rows, int64_t Np, int64_t nplanes,
+              int64_t plane_elems, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)rows, (cuuint64_t)nplanes};
+  cuuint64_t strides[2] = {(cuuint64_t)Np * 2, (cuuint64_t)plane_elems * 2};
+  cuuint32_t box[3] = {(cuuint32_t)TC_KC, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int d = 0;
+    cudaGetDevice(&d);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+    if (n < 1) n = 1;
+  }
+  return n;
+}
+
+cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vector<int4>& tiles, TcParams p,
+                   void* scratch, size_t scratch_bytes, cudaStream_t s) {
+  if (tiles.empty()) return cudaSuccess;
+  const size_t tbytes = tiles.size() * sizeof(int4);
+  if (tbytes > scratch_bytes) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(scratch, tiles.data(), tbytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  p.tiles = (const int4*)scratch;
+  p.ntiles = (int)tiles.size();
+  const size_t smem = sizeof(TcSmem) + 1024;
+  e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min<int>((int)tiles.size(), sm_count());
+  tc_gemm_kernel<<<grid, TC_THREADS, smem, s>>>(mA, mB, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fg_tc_available() {
+  static int avail = -1;
+  if (avail < 0) {
+    int d = 0, major = 0, minor = 0;
+    avail = 0;
+    if (cudaGetDevice(&d) == cudaSuccess &&
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, d) == cudaSuccess &&
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, d) == cudaSuccess)
+      avail = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
+  }
+  return avail == 1;
+}
+
+int64_t fg_tc_signal_rows(int64_t B, int64_t) { return B; }
+
+size_t fg_tc_scratch_bytes(int64_t N, int64_t B, int64_t groups, int) {
+  const int64_t row_tiles = (N + TC_BM - 1) / TC_BM;
+  const int64_t col_tiles = (B + TC_BN - 1) / TC_BN + groups;  // each group may add a ragged tile
+  return (size_t)(row_tiles * col_tiles) * sizeof(int4) + 256;
+}
+
+cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
+  if (a.N > (1 << 24) || a.B > (1 << 30)) return cudaErrorInvalidValue;
+  cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s);
+  if (e != cudaSuccess) return e;
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, a.Qs, a.N, a.N, a.Np, 4 * a.groups, a.plane_elems, TC_BM) ||
+      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN))
+    return cudaErrorInvalidValue;
+  std::vector<int4> tiles;
+  const int row_tiles = (int)((a.N + TC_BM - 1) / TC_BM);
+  for (int64_t g = 0; g < a.groups; ++g) {
+    const int64_t c0 = a.gstart[g], c1 = a.gstart[g] + a.gcount[g];
+    for (int rt = 0; rt < row_tiles; ++rt)
+      for (int64_t c = c0; c < c1; c += TC_BN)
+        tiles.push_back(make_int4(rt, (int)(4 * g), (int)c, (int)std::min<int64_t>(c + TC_BN, c1)));
+  }
+  TcParams p{};
+  p.nblk = 1;
+  p.grouped = 1;
+  p.N = (int)a.N;
+  p.kchunks = (int)((a.N + TC_KC - 1) / TC_KC);
+  p.Y = a.Y;
+  p.col_exp = a.col_exp;
+  p.status = a.status;
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s);
+}
+
+cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
+  if (a.N > (1 << 24) || a.B > (1 << 30)) return cudaErrorInvalidValue;
+  cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s);
+  if (e != cudaSuccess) return e;
+  CUtensorMap mA, mB;
+  const int64_t nplanes = 4 * (int64_t)(std::max(a.b0 + a.nb_pow, a.p_blk + 1));
+  if (!make_map(&mA, a.stack, a.N, a.N, a.Np, nplanes, a.plane_elems, TC_BM) ||
+      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN))
+    return cudaErrorInvalidValue;
+  std::vector<int4> tiles;
+  const int row_tiles = (int)((a.N + TC_BM - 1) / TC_BM);
+  for (int rt = 0; rt < row_tiles; ++rt)
+    for (int64_t c = 0; c < a.B; c += TC_BN)
+      tiles.push_back(make_int4(rt, 0, (int)c, (int)std::min<int64_t>(c + TC_BN, a.B)));
+  TcParams p{};
+  p.nblk = a.nb_pow + (a.p_blk >= 0 ? 1 : 0);
+  p.grouped = 0;
+  p.b0 = a.b0;
+  p.nb_pow = a.nb_pow;
+  p.p_blk = a.p_blk;
+  p.N = (int)a.N;
+  p.kchunks = (int)((a.N + TC_KC - 1) / TC_KC);
+  p.coef = a.coef;
+  p.coefd = a.coefd;
+  p.ldcoef = a.B;
+  p.Y = a.Y;
+  p.D = a.D;
+  p.col_exp = a.col_exp;
+  p.status = a.status;
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s);
+}

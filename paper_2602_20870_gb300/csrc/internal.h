@@ -1,0 +1,192 @@
+// Internal declarations shared by the libfgfrft translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "fgfrft.h"
+
+// ---------------------------------------------------------------------------
+// plan record (host side; the device memory it points into belongs to the caller)
+// ---------------------------------------------------------------------------
+struct fgfrft_plan_s {
+  int64_t N;
+  int L_max;
+  int storage;
+  int nblk;            // 2 * L_max + 2: M_{-L_max} .. M_{L_max}, then P
+  int64_t blk_elems;   // c64 entries per block (N*N padded to 32)
+  int64_t Np;          // fp16 row pitch in elements (N rounded up to 8, 16-byte rows)
+  int64_t plane_elems; // fp16 entries per plane (N * Np, padded to 128)
+  size_t bytes;
+  uint32_t* dstatus;   // device status word (bit set of kernel error codes)
+  float2* c64;         // [nblk][blk_elems] or NULL
+  __half* f16;         // [nblk][4][plane_elems] or NULL; planes re_hi, re_lo, im_hi, im_lo
+  int r_neg1;
+  double proj_residual;
+  int squarings;
+};
+
+// Index of the stored block holding M_l (l in -L_max..L_max) and of P.
+static inline int blk_of_power(const fgfrft_plan_s* p, int l) { return p->L_max + l; }
+static inline int blk_of_P(const fgfrft_plan_s* p) { return 2 * p->L_max + 1; }
+
+// Scale applied to stored entries before the fp16 hi/lo split (exact power of two):
+// entries of the partial isometries F^l P_c and of Q are at most ~1.2 in magnitude,
+// so 2^12 keeps hi below the fp16 maximum and lo in the normal range for typical
+// entries (~N^{-1/2}).
+#define FG_SPLIT_SHIFT 12
+// Signals are scaled per column by 2^e so that max |x| * 2^e lies in [2^13, 2^14).
+#define FG_X_TARGET_EXP 13
+
+// Device status codes (OR-ed into the plan's status word).
+#define FG_STATUS_WAIT_TIMEOUT 1u
+
+// Bounded waits give up after this many nanoseconds of %globaltimer.
+#define FG_WAIT_LIMIT_NS 2000000000ull
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete, for at most
+// FG_WAIT_LIMIT_NS.  On timeout, record it in *status and return false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_timer_ns() - t0 > FG_WAIT_LIMIT_NS) {
+      atomicOr(status, FG_STATUS_WAIT_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// 1-D bulk copy global -> shared, completion counted in bytes on *bar.
+// dst and src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s_evict_first(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                     uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+      "%4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+#endif  // __CUDACC__
+
+// ---------------------------------------------------------------------------
+// launchers (one translation unit each)
+// ---------------------------------------------------------------------------
+// offline.cu
+cudaError_t fg_zgemm(bool transA, bool transB, int M, int N, int K, double2 alpha, const double2* A, int lda,
+                     const double2* B, int ldb, double2 beta, double2* C, int ldc, cudaStream_t s);
+cudaError_t fg_zaxpby_identity(int64_t N, double2 a, const double2* X, double2 b, double2 d, double2* Y,
+                               cudaStream_t s);  // Y = a*X + b*Y + d*I
+cudaError_t fg_zherm_sym(int64_t N, double2* S, cudaStream_t s);  // S <- (S + S^H)/2
+cudaError_t fg_zmcweeny(int64_t N, const double2* P2, const double2* P3, double2* P, cudaStream_t s);
+cudaError_t fg_ztrace_fro(int64_t N, const double2* S, const double2* Sub, double* out, cudaStream_t s);
+cudaError_t fg_store_block(int64_t N, const double2* M, bool conj_transpose, float2* c64, __half* f16,
+                           int64_t Np, int64_t plane_elems, cudaStream_t s);
+
+// assemble.cu
+cudaError_t fg_assemble_single(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk,
+                               int64_t NN, const float2* coef, float2* Q, uint32_t* status, cudaStream_t s);
+// Multi-order: Q_a = sum_b coef[b * A + a] * block_b for a < A; output c64 (Qc) or split fp16 (Qs).
+cudaError_t fg_assemble_multi(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk,
+                              int64_t N, int A, const float2* coef, float2* Qc, __half* Qs, int64_t Np,
+                              int64_t plane_elems, uint32_t* status, cudaStream_t s);
+
+// gemm_simt.cu: Y[j][i] (+)= sum_b coef[b][j] * sum_k A_b[i][k] X[j][k]   (FP32 CUDA cores)
+struct SimtStackArgs {
+  const float2* A;       // block b starts at A + blk_index(b) * blk_elems, rows of lda entries
+  int64_t blk_elems;
+  int lda;
+  int b0, nb_pow, p_blk; // blocks b0 .. b0+nb_pow-1, then p_blk (p_blk < 0: none)
+  int N;                 // rows of A and length of each signal
+  int ncols;             // columns (signals) handled
+  const float2* X;       // signal j at X + j * N
+  float2* Y;             // output signal j at Y + j * N
+  float2* D;             // dual output or NULL
+  const float2* coef;    // [nblk][ldcoef] or NULL (unscaled single block)
+  const float2* coefd;   // [nblk][ldcoef] for D
+  int ldcoef;
+};
+cudaError_t fg_simt_stacked(const SimtStackArgs& a, cudaStream_t s);
+
+// reduce.cu
+// coefficient (b, j) at b * ldb + j * ldj; blocks b = 0..2L are the powers -L..L, b = 2L+1 is P
+cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* coef, float2* coefd, int64_t ldb,
+                      int64_t ldj, cudaStream_t s);
+int fg_grad_chunks(int64_t N);
+cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N, float* out, double* partials,
+                          cudaStream_t s);
+cudaError_t fg_split_signals(const float2* X, int64_t B, int64_t N, int64_t Np, int64_t rows_pad, __half* planes,
+                             int* col_exp, cudaStream_t s);

@@ -1,0 +1,51 @@
+// Tensor-core (tcgen05) GEMM paths: split-fp16 operands, FP32 accumulators in TMEM.
+#pragma once
+#include "internal.h"
+
+// True when the tcgen05 kernels are compiled in and the current device is sm_103.
+bool fg_tc_available();
+// Rows of the signal split planes for B signals in the given number of groups
+// (padded so that every TMA box row stays inside the buffer).
+int64_t fg_tc_signal_rows(int64_t B, int64_t groups);
+// Device scratch (tile tables, partial sums) of one call.
+size_t fg_tc_scratch_bytes(int64_t N, int64_t B, int64_t groups, int nblk);
+
+// Y[:, group g] = Q_g X[:, group g] for consecutive column groups (assembled path).
+struct TcGroupedArgs {
+  int64_t N, Np, plane_elems;
+  const __half* Qs;        // [groups][4][plane_elems] split operators (scaled by 2^FG_SPLIT_SHIFT)
+  int64_t groups;
+  const int64_t* gstart;   // host: first column of each group
+  const int64_t* gcount;   // host: columns of each group
+  const float2* X;         // B x N signals
+  float2* Y;               // B x N outputs
+  __half* Xs;              // work: [4][xs_rows][Np] split signals
+  int64_t xs_rows;
+  int* col_exp;            // work: [xs_rows]
+  int64_t B;
+  void* scratch;
+  size_t scratch_bytes;
+  uint32_t* status;
+};
+cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s);
+
+// Y[:, j] = sum_b coef[b][j] A_b X[:, j] over the stored blocks (stacked path),
+// D likewise with coefd (dual accumulator, may be NULL).
+struct TcStackedArgs {
+  int64_t N, Np, plane_elems;
+  const __half* stack;     // [nblk_total][4][plane_elems]
+  int b0, nb_pow, p_blk;
+  const float2* X;
+  float2* Y;
+  float2* D;
+  const float2* coef;      // [nb_pow + 1][B]
+  const float2* coefd;
+  int64_t B;
+  __half* Xs;
+  int64_t xs_rows;
+  int* col_exp;
+  void* scratch;
+  size_t scratch_bytes;
+  uint32_t* status;
+};
+cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s);

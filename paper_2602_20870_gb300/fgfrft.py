@@ -1,0 +1,290 @@
+"""Thin Python binding of libfgfrft (ctypes).
+
+Argument marshalling only: every step of the transform runs in the library's
+CUDA kernels.  PyTorch provides device memory and the current CUDA stream.
+The library must have been built (``paper_2602_20870_gb300.build.build()``);
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from .build import LIB
+
+# enum values mirrored from include/fgfrft.h
+OK = 0
+ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_NOT_UNITARY, ERR_AMBIGUOUS_SPECTRUM = 1, 2, 3, 4
+ERR_NO_MEMORY, ERR_CUDA, ERR_TIMEOUT = 5, 6, 7
+STORE_C64, STORE_SPLIT_F16 = 1, 2
+ADJOINT, SHARED_ALPHA = 1, 2
+PATH_PLAIN, PATH_ASSEMBLED, PATH_STACKED, PATH_STACKED_FP32 = 0x10, 0x20, 0x40, 0x80
+OP_ASSEMBLE, OP_APPLY, OP_GRAD = 1, 2, 3
+
+PATHS = {"auto": 0, "plain": PATH_PLAIN, "assembled": PATH_ASSEMBLED, "stacked": PATH_STACKED,
+         "stacked_fp32": PATH_STACKED_FP32}
+
+# exported entry points and their ctypes signatures
+_vp, _i64, _i32, _sz, _dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t, ctypes.c_double
+SIGNATURES = {
+    "fgfrft_strerror": (ctypes.c_char_p, [_i32]),
+    "fgfrft_version": (_i32, []),
+    "fgfrft_plan_bytes": (_sz, [_i64, _i32, _i32]),
+    "fgfrft_precompute_work_bytes": (_sz, [_i64]),
+    "fgfrft_precompute": (_i32, [_vp, _i64, _i32, _i32, _vp, _i64, _vp, _sz, _vp, _sz, _vp,
+                                 ctypes.POINTER(_vp)]),
+    "fgfrft_plan_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                ctypes.POINTER(_i32), ctypes.POINTER(_dp), ctypes.POINTER(_i32),
+                                ctypes.POINTER(_sz)]),
+    "fgfrft_plan_block": (_vp, [_vp, _i32, _i32, ctypes.POINTER(_i64)]),
+    "fgfrft_plan_status": (_i32, [_vp, _vp]),
+    "fgfrft_plan_destroy": (_i32, [_vp]),
+    "fgfrft_work_bytes": (_sz, [_vp, _i32, _vp, _i64, _i32, _i32]),
+    "fgfrft_assemble": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _sz, _vp]),
+    "fgfrft_apply": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp, _sz, _vp]),
+    "fgfrft_grad": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp]),
+}
+
+
+class FGFRFTError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {_lib().fgfrft_strerror(code).decode()} (status {code})")
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"libfgfrft.so is not built ({LIB}); run paper_2602_20870_gb300.build.build()")
+        lib = ctypes.CDLL(LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def load():
+    """Load libfgfrft.so (raises ImportError if it is not built)."""
+    return _lib()
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise FGFRFTError(rc, where)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _alpha_array(alpha, count=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(-1))
+    if count is not None and a.size == 1 and count > 1:
+        a = np.full(count, float(a[0]))
+    return a
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Plan:
+    """Offline part of Algorithm 1 on the GPU, and the online calls on its stack.
+
+    ``F`` is an N x N unitary matrix (numpy or torch, converted to complex128 on
+    the device).  The plan's device memory is a torch uint8 tensor owned here.
+    """
+
+    def __init__(self, F, L_max: int, storage: int = STORE_C64 | STORE_SPLIT_F16, W=None,
+                 device="cuda", stream=None):
+        lib = _lib()
+        Ft = torch.as_tensor(np.asarray(F) if not torch.is_tensor(F) else F)
+        Ft = Ft.to(device=device, dtype=torch.complex128).contiguous()
+        N = Ft.shape[0]
+        if Ft.shape != (N, N):
+            raise ValueError("F must be square")
+        self.N, self.L_max, self.storage, self.device = int(N), int(L_max), int(storage), torch.device(device)
+        nbytes = lib.fgfrft_plan_bytes(N, L_max, storage)
+        if nbytes == 0:
+            raise FGFRFTError(ERR_INVALID_ARG, "fgfrft_plan_bytes")
+        self.mem = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        wbytes = lib.fgfrft_precompute_work_bytes(N)
+        work = torch.empty(wbytes, dtype=torch.uint8, device=device)
+        Wt = None
+        r = 0
+        if W is not None:
+            Wt = torch.as_tensor(np.asarray(W) if not torch.is_tensor(W) else W).to(
+                device=device, dtype=torch.complex128).contiguous()
+            r = Wt.shape[1] if Wt.ndim == 2 else 0
+        h = ctypes.c_void_p()
+        rc = lib.fgfrft_precompute(_ptr(Ft), N, L_max, storage, _ptr(Wt), r, _ptr(self.mem), nbytes,
+                                   _ptr(work), wbytes, ctypes.c_void_p(_stream(stream)), ctypes.byref(h))
+        _check(rc, "fgfrft_precompute")
+        self._h = h
+        del work
+        n64, lm, st, rn, sq, pb = _i64(), _i32(), _i32(), _i32(), _i32(), _sz()
+        res = _dp()
+        _check(lib.fgfrft_plan_info(h, ctypes.byref(n64), ctypes.byref(lm), ctypes.byref(st), ctypes.byref(rn),
+                                    ctypes.byref(res), ctypes.byref(sq), ctypes.byref(pb)), "fgfrft_plan_info")
+        self.r_neg1, self.proj_residual, self.squarings, self.plan_bytes = rn.value, res.value, sq.value, pb.value
+        self._work = None
+
+    # ---------------------------------------------------------------- helpers
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().fgfrft_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def work_tensor(self, op: int, alpha: np.ndarray, count: int, L: int, flags: int) -> torch.Tensor:
+        n = _lib().fgfrft_work_bytes(self._h, op, alpha.ctypes.data_as(ctypes.c_void_p), count, L, flags)
+        if n == 0:
+            # invalid request: the call itself reports the precise status before using the buffer
+            n = 256
+        if self._work is None or self._work.numel() < n:
+            self._work = torch.empty(n, dtype=torch.uint8, device=self.device)
+        return self._work
+
+    def block(self, l: int, storage: int = STORE_C64) -> torch.Tensor:
+        """Stored block M_l (l in -L_max..L_max) or P (l = L_max + 1) as a device tensor view."""
+        stride = _i64()
+        ptr = _lib().fgfrft_plan_block(self._h, storage, l, ctypes.byref(stride))
+        if not ptr:
+            raise FGFRFTError(ERR_INVALID_ARG, "fgfrft_plan_block")
+        base = self.mem.data_ptr()
+        off = ptr - base
+        if storage == STORE_C64:
+            nbytes = self.N * self.N * 8
+            return self.mem[off:off + nbytes].view(torch.complex64).view(self.N, self.N)
+        Np = (self.N + 7) // 8 * 8
+        pe = stride.value // 4
+        planes = self.mem[off:off + stride.value * 2].view(torch.float16).view(4, pe)
+        return planes[:, : self.N * Np].reshape(4, self.N, Np)[:, :, : self.N]
+
+    def status(self, stream=None):
+        _check(_lib().fgfrft_plan_status(self._h, ctypes.c_void_p(_stream(stream))), "fgfrft_plan_status")
+
+    # ---------------------------------------------------------------- online
+    def assemble(self, alpha, L: int | None = None, out: torch.Tensor | None = None, stream=None):
+        """Q_L^{alpha_a} for each order (Def. 1), complex64 (A, N, N)."""
+        L = self.L_max if L is None else int(L)
+        a = _alpha_array(alpha)
+        A = a.size
+        if out is None:
+            out = torch.empty((A, self.N, self.N), dtype=torch.complex64, device=self.device)
+        w = self.work_tensor(OP_ASSEMBLE, a, A, L, 0)
+        rc = _lib().fgfrft_assemble(self._h, a.ctypes.data_as(ctypes.c_void_p), A, L, _ptr(out), _ptr(w),
+                                    w.numel(), ctypes.c_void_p(_stream(stream)))
+        _check(rc, "fgfrft_assemble")
+        return out
+
+    def apply(self, alpha, X: torch.Tensor, L: int | None = None, adjoint: bool = False, path: str = "auto",
+              out: torch.Tensor | None = None, stream=None):
+        """Y[j] = Q_L^{alpha_j} X[j] (Def. 2), X of shape (B, N), one signal per row.
+
+        A CPU ``X`` is copied to the device and the result copied back (end to end)."""
+        L = self.L_max if L is None else int(L)
+        host = X.device.type == "cpu"
+        Xd = X.to(self.device, dtype=torch.complex64, non_blocking=True).contiguous() if host or \
+            X.dtype != torch.complex64 else X.contiguous()
+        B = Xd.shape[0]
+        a = _alpha_array(alpha, B)
+        flags = PATHS[path] | (ADJOINT if adjoint else 0)
+        Y = torch.empty_like(Xd) if (out is None or host) else out
+        w = self.work_tensor(OP_APPLY, a, B, L, flags)
+        rc = _lib().fgfrft_apply(self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, _ptr(Xd), _ptr(Y), flags,
+                                 _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream)))
+        _check(rc, "fgfrft_apply")
+        if host:
+            dst = out if out is not None else torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True)
+            dst.copy_(Y, non_blocking=True)
+            return dst
+        return Y
+
+    def forward_dual(self, alpha, X: torch.Tensor, L: int | None = None, path: str = "auto", stream=None):
+        """(Y, dY/dalpha) from one pass over the stored powers (Prop. 3)."""
+        L = self.L_max if L is None else int(L)
+        X = X.contiguous()
+        B = X.shape[0]
+        a = _alpha_array(alpha, B)
+        flags = PATHS[path]
+        Y = torch.empty_like(X)
+        D = torch.empty_like(X)
+        w = self.work_tensor(OP_GRAD, a, B, L, flags)
+        rc = _lib().fgfrft_grad(self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, _ptr(X), _ptr(Y), _ptr(D),
+                                None, None, None, flags, _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream)))
+        _check(rc, "fgfrft_grad(forward)")
+        return Y, D
+
+    def backward(self, alpha, G: torch.Tensor, D: torch.Tensor | None, L: int | None = None,
+                 need_x: bool = True, path: str = "auto", stream=None):
+        """(Q^H G, Re <G, D> per column) (Props. 2-3 and the chain rule)."""
+        L = self.L_max if L is None else int(L)
+        G = G.contiguous()
+        B = G.shape[0]
+        a = _alpha_array(alpha, B)
+        flags = PATHS[path]
+        gX = torch.empty_like(G) if need_x else None
+        ga = torch.empty(B, dtype=torch.float32, device=G.device) if D is not None else None
+        w = self.work_tensor(OP_GRAD, a, B, L, flags)
+        rc = _lib().fgfrft_grad(self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, None, None, _ptr(D),
+                                _ptr(G), _ptr(gX), _ptr(ga), flags, _ptr(w), w.numel(),
+                                ctypes.c_void_p(_stream(stream)))
+        _check(rc, "fgfrft_grad(backward)")
+        return gX, ga
+
+
+class FGFRFTFunction(torch.autograd.Function):
+    """Y = Q_L^{alpha} X with a hand-written backward (Props. 2-3).
+
+    alpha: float64 tensor of shape (B,) (one order per signal row of X) or (1,);
+    X: complex64 (B, N) on the plan's device.  The forward computes Y and dY/dalpha
+    in one pass; the backward returns Q^H G and Re <G, dY/dalpha>."""
+
+    @staticmethod
+    def forward(ctx, alpha: torch.Tensor, X: torch.Tensor, plan: Plan, L: int, path: str = "auto"):
+        B = X.shape[0]
+        a = alpha.detach().to("cpu", torch.float64).numpy()
+        Y, D = plan.forward_dual(a, X, L, path)
+        ctx.plan, ctx.L, ctx.path, ctx.a = plan, L, path, a
+        ctx.alpha_device, ctx.alpha_dtype = alpha.device, alpha.dtype
+        ctx.shared = alpha.numel() == 1 and B > 1
+        ctx.save_for_backward(D)
+        return Y
+
+    @staticmethod
+    def backward(ctx, G):
+        (D,) = ctx.saved_tensors
+        need_x = ctx.needs_input_grad[1]
+        gX, ga = ctx.plan.backward(ctx.a, G.to(torch.complex64), D, ctx.L, need_x, ctx.path)
+        galpha = None
+        if ctx.needs_input_grad[0]:
+            galpha = ga.to(device=ctx.alpha_device, dtype=ctx.alpha_dtype)
+            if ctx.shared:
+                galpha = galpha.sum().reshape(1)
+        return galpha, gX, None, None, None
+
+
+def fgfrft(alpha: torch.Tensor, X: torch.Tensor, plan: Plan, L: int | None = None, path: str = "auto"):
+    """Differentiable FGFRFT: Q_L^{alpha} X (autograd through alpha and X)."""
+    return FGFRFTFunction.apply(alpha, X, plan, plan.L_max if L is None else int(L), path)
