@@ -73,6 +73,11 @@ enum fgfrft_storage {
   FGFRFT_STORE_SPLIT_F16 = 2, /* blocks as four fp16 planes {re_hi, re_lo, im_hi, im_lo}
                                  of the entries scaled by 2^12, 8 B per entry:
                                  tensor-core paths */
+  FGFRFT_STORE_ENTRY_F16 = 4, /* an entry-major copy of the split planes: for every entry
+                                 of the N x N blocks, all 2 L_max + 2 stored blocks
+                                 contiguous (row pitch rounded up to 8); lets the fused
+                                 multi-order assembly run as one tensor-core GEMM.
+                                 Requires FGFRFT_STORE_SPLIT_F16. */
 };
 
 /* Flags of fgfrft_apply / fgfrft_grad. */
@@ -100,7 +105,8 @@ int fgfrft_version(void);
 /* Bytes of device memory a plan for (N, L_max, storage) occupies: the status
  * word, 2 L_max + 2 blocks of N x N entries (M_{-L_max} .. M_{L_max}, then P)
  * in every storage requested, each block padded to 256 B.  Returns 0 for
- * invalid arguments (N < 1, L_max < 0, no known storage bit). */
+ * invalid arguments (N < 1, L_max < 0, no known storage bit, or
+ * FGFRFT_STORE_ENTRY_F16 without FGFRFT_STORE_SPLIT_F16). */
 size_t fgfrft_plan_bytes(int64_t N, int L_max, int storage);
 
 /* Bytes of FP64 device scratch fgfrft_precompute needs: 3 N^2 complex128
@@ -167,8 +173,11 @@ size_t fgfrft_work_bytes(fgfrft_plan p, int op, const double* alpha_host, int64_
  * Online part of Algorithm 1 (Def. 1), A orders in one pass over the stack.
  *   alpha_host  A orders.
  *   Q_dev       A x N x N c64 output, Q_dev[a][i][k] = (Q_L^{alpha_a})_{ik}.
- * A = 1 streams the 2L + 2 stored blocks once with bulk-copy staging; A > 1
- * reads each stored entry once for all A outputs.  Needs FGFRFT_STORE_C64.
+ * A = 1 streams the 2L + 2 stored c64 blocks once with bulk-copy staging
+ * (needs FGFRFT_STORE_C64).  A > 1 reads each stored entry once for all A
+ * outputs: as one tensor-core GEMM over the entry-major split stack when the plan
+ * has FGFRFT_STORE_ENTRY_F16 (split-fp16 products, FP32 accumulation), else on
+ * FP32 CUDA cores from the c64 stack.
  */
 int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L,
                     void* Q_dev, void* work, size_t work_bytes, void* stream);
@@ -202,6 +211,28 @@ int fgfrft_grad(fgfrft_plan p, const double* alpha_host, int64_t B, int L,
                 const void* X_dev, void* Y_dev, void* dY_dev,
                 const void* G_dev, void* gradX_dev, float* gradalpha_dev,
                 int flags, void* work, size_t work_bytes, void* stream);
+
+/* Kernel classes for launch counting and timing. */
+enum fgfrft_kernel_class {
+  FGFRFT_KC_COEFFS = 0,          /* per-column coefficients (FP64 on the device) */
+  FGFRFT_KC_ASSEMBLE_SINGLE = 1, /* one-order assembly, bulk-copy streaming */
+  FGFRFT_KC_ASSEMBLE_MULTI = 2,  /* fused multi-order assembly (CUDA-core or tensor-core kernel) */
+  FGFRFT_KC_SPLIT_SIGNALS = 3,   /* fp16 hi/lo split of signal columns */
+  FGFRFT_KC_TC_GEMM = 4,         /* tcgen05 stacked / grouped GEMM */
+  FGFRFT_KC_SIMT_GEMM = 5,       /* FP32 CUDA-core GEMM */
+  FGFRFT_KC_GRAD_REDUCE = 6,     /* alpha-gradient reduction */
+  FGFRFT_KC_OFFLINE = 7,         /* FP64 offline kernels */
+  FGFRFT_KC_COUNT = 8
+};
+
+/* Process-wide instrumentation.  Launch counts are always kept.  While timing is
+ * enabled, every call that launches kernels of a class records a CUDA event pair
+ * around those launches on the call's stream (at most 65536 pairs per class
+ * between resets).  fgfrft_timing_read synchronises on the recorded events and
+ * returns the launches, the timed calls and the summed device time in ms. */
+int fgfrft_timing_enable(int on);
+int fgfrft_timing_reset(void);
+int fgfrft_timing_read(int kernel_class, int64_t* launches, int64_t* timed_calls, double* total_ms);
 
 #ifdef __cplusplus
 }

@@ -18,8 +18,8 @@ inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 struct Layout {
-  int64_t blk_elems, Np, plane_elems;
-  size_t off_c64, off_f16, total;
+  int64_t blk_elems, Np, plane_elems, Kp, planeT;
+  size_t off_c64, off_f16, off_f16T, total;
 };
 
 Layout plan_layout(int64_t N, int L_max, int storage) {
@@ -33,6 +33,10 @@ Layout plan_layout(int64_t N, int L_max, int storage) {
   if (storage & FGFRFT_STORE_C64) off = align_up(off + (size_t)nblk * l.blk_elems * sizeof(float2));
   l.off_f16 = off;
   if (storage & FGFRFT_STORE_SPLIT_F16) off = align_up(off + (size_t)nblk * 4 * l.plane_elems * sizeof(__half));
+  l.Kp = round_up(nblk, 8);
+  l.planeT = round_up(N * N * l.Kp, 128);
+  l.off_f16T = off;
+  if (storage & FGFRFT_STORE_ENTRY_F16) off = align_up(off + (size_t)4 * l.planeT * sizeof(__half));
   l.total = off;
   return l;
 }
@@ -100,6 +104,73 @@ int choose_path(const fgfrft_plan_s* p, const std::vector<double>& a, int flags)
   return tensor ? FGFRFT_PATH_STACKED : FGFRFT_PATH_STACKED_FP32;
 }
 
+// Work layout of fgfrft_assemble (and of the assembly stage of the assembled path).
+struct AssembleWork {
+  double* alpha_dev = nullptr;
+  float2* coef = nullptr;    // SIMT: [2L+2][A]; tensor: [A][nblk] order-major, zero outside -L..L
+  __half* Cs = nullptr;      // tensor: split coefficients [4][A][Kp]
+  int* col_exp = nullptr;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  bool tensor = false;
+  size_t bytes = 0;
+};
+
+AssembleWork carve_assemble(const fgfrft_plan_s* p, char* base, int64_t A, int L) {
+  AssembleWork w;
+  Carve c{base};
+  w.tensor = p->f16T != nullptr && A >= 2 && fg_tc_available();
+  w.alpha_dev = c.take<double>((size_t)A);
+  if (w.tensor) {
+    w.coef = c.take<float2>((size_t)A * p->nblk);
+    w.Cs = c.take<__half>((size_t)4 * A * p->Kp);
+    w.col_exp = c.take<int>((size_t)A);
+    w.scratch_bytes = fg_tc_assemble_scratch_bytes(p->N * p->N, A);
+    w.scratch = c.take<char>(w.scratch_bytes);
+  } else {
+    w.coef = c.take<float2>((size_t)(2 * L + 2) * A);
+  }
+  w.bytes = c.off;
+  return w;
+}
+
+// Enqueue the fused assembly of A orders into Qc (c64 [A][N*N]) or Qs (split planes).
+cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const double* alpha_dev, int64_t A, int L,
+                         float2* Qc, __half* Qs, cudaStream_t s) {
+  const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
+  if (w.tensor) {
+    cudaError_t e = cudaMemsetAsync(w.coef, 0, (size_t)A * p->nblk * sizeof(float2), s);
+    if (e != cudaSuccess) return e;
+    e = fg_coeffs_stored(alpha_dev, (int)A, L, p->L_max, false, w.coef, 1, p->nblk, s);
+    if (e != cudaSuccess) return e;
+    TcAssembleArgs ta{};
+    ta.entry_stack = p->f16T;
+    ta.entries = p->N * p->N;
+    ta.K = p->nblk;
+    ta.Kp = p->Kp;
+    ta.planeT = p->planeT;
+    ta.coefT = w.coef;
+    ta.A = A;
+    ta.Cs = w.Cs;
+    ta.col_exp = w.col_exp;
+    ta.Qc = Qc;
+    ta.Qs = Qs;
+    ta.N = p->N;
+    ta.Np = p->Np;
+    ta.plane_elems = p->plane_elems;
+    ta.scratch = w.scratch;
+    ta.scratch_bytes = w.scratch_bytes;
+    ta.status = p->dstatus;
+    return fg_tc_assemble(ta, s);
+  }
+  cudaError_t e = fg_coeffs(alpha_dev, (int)A, L, false, w.coef, nullptr, A, 1, s);
+  if (e != cudaSuccess) return e;
+  if (A == 1 && Qs == nullptr)
+    return fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, w.coef, Qc, p->dstatus, s);
+  return fg_assemble_multi(p->c64, p->blk_elems, b0, nb, pb, p->N, (int)A, w.coef, Qc, Qs, p->Np, p->plane_elems,
+                           p->dstatus, s);
+}
+
 // Work layout of an apply / grad call; base == nullptr computes the size only.
 struct ApplyWork {
   double* alpha_dev = nullptr;
@@ -114,6 +185,8 @@ struct ApplyWork {
   void* tc_scratch = nullptr;
   size_t tc_scratch_bytes = 0;
   int64_t xs_rows = 0;
+  AssembleWork asm_work;
+  char* asm_base = nullptr;
   size_t bytes = 0;
 };
 
@@ -132,16 +205,19 @@ ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int 
       w.coef = c.take<float2>((size_t)nb * B);
       w.coefd = c.take<float2>((size_t)nb * B);
       break;
-    case FGFRFT_PATH_ASSEMBLED:
+    case FGFRFT_PATH_ASSEMBLED: {
       w.group_alpha_dev = c.take<double>((size_t)groups);
-      w.coef = c.take<float2>((size_t)nb * groups);
+      w.asm_work = carve_assemble(p, nullptr, groups, L);
+      w.asm_base = c.take<char>(w.asm_work.bytes);
       w.Qs = c.take<__half>((size_t)groups * 4 * p->plane_elems);
       w.xs_rows = fg_tc_signal_rows(B, groups);
       w.Xs = c.take<__half>((size_t)4 * w.xs_rows * p->Np);
       w.col_exp = c.take<int>((size_t)w.xs_rows);
       w.tc_scratch_bytes = fg_tc_scratch_bytes(p->N, B, groups, 1);
       w.tc_scratch = c.take<char>(w.tc_scratch_bytes);
+      if (base) w.asm_work = carve_assemble(p, w.asm_base, groups, L);
       break;
+    }
     case FGFRFT_PATH_STACKED:
       w.coef = c.take<float2>((size_t)nb * B);
       w.coefd = c.take<float2>((size_t)nb * B);
@@ -183,8 +259,10 @@ int fgfrft_version(void) { return 100; }
 
 size_t fgfrft_plan_bytes(int64_t N, int L_max, int storage) {
   if (N < 1 || N > 65536 || L_max < 0 || L_max > 1000) return 0;
+  const int known = FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16 | FGFRFT_STORE_ENTRY_F16;
   if ((storage & (FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16)) == 0) return 0;
-  if (storage & ~(FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16)) return 0;
+  if (storage & ~known) return 0;
+  if ((storage & FGFRFT_STORE_ENTRY_F16) && !(storage & FGFRFT_STORE_SPLIT_F16)) return 0;
   return plan_layout(N, L_max, storage).total;
 }
 
@@ -220,6 +298,9 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   p->dstatus = (uint32_t*)pm;
   p->c64 = (storage & FGFRFT_STORE_C64) ? (float2*)(pm + lay.off_c64) : nullptr;
   p->f16 = (storage & FGFRFT_STORE_SPLIT_F16) ? (__half*)(pm + lay.off_f16) : nullptr;
+  p->f16T = (storage & FGFRFT_STORE_ENTRY_F16) ? (__half*)(pm + lay.off_f16T) : nullptr;
+  p->Kp = lay.Kp;
+  p->planeT = lay.planeT;
 
   const int n = (int)N;
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
@@ -318,6 +399,8 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
     if (!store(blk_of_power(p, k), nxt, false) || !store(blk_of_power(p, -k), nxt, true)) return fail(FGFRFT_ERR_CUDA);
     std::swap(cur, nxt);
   }
+  if (p->f16T && fg_entry_major(p->f16, p->nblk, N, p->Np, p->plane_elems, p->f16T, p->Kp, p->planeT, s))
+    return fail(FGFRFT_ERR_CUDA);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FGFRFT_ERR_CUDA);
   *out = p;
   return FGFRFT_OK;
@@ -375,7 +458,7 @@ size_t fgfrft_work_bytes(fgfrft_plan p, int op, const double* alpha_host, int64_
   std::vector<double> a;
   if (op == FGFRFT_OP_ASSEMBLE) {
     if (!alpha_host) return 0;
-    return align_up((size_t)count * sizeof(double)) + align_up((size_t)(2 * L + 2) * count * sizeof(float2));
+    return carve_assemble(p, nullptr, count, L).bytes;
   }
   if (gather_orders(alpha_host, count, L, flags, a) != FGFRFT_OK) return 0;
   if (flags & FGFRFT_ADJOINT)
@@ -393,7 +476,7 @@ size_t fgfrft_work_bytes(fgfrft_plan p, int op, const double* alpha_host, int64_
 int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, void* Q_dev, void* work,
                     size_t work_bytes, void* stream) {
   if (!p || !alpha_host || A < 1 || !Q_dev || !work || L < 0) return FGFRFT_ERR_INVALID_ARG;
-  if (L > p->L_max || !p->c64) return FGFRFT_ERR_UNSUPPORTED;
+  if (L > p->L_max) return FGFRFT_ERR_UNSUPPORTED;
   if (A > 65535) return FGFRFT_ERR_INVALID_ARG;
   std::vector<double> a;
   int rc = gather_orders(alpha_host, A, L, 0, a);
@@ -402,17 +485,10 @@ int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, v
       !aligned(Q_dev, 16))
     return FGFRFT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  Carve c{(char*)work};
-  double* alpha_dev = c.take<double>((size_t)A);
-  float2* coef = c.take<float2>((size_t)(2 * L + 2) * A);
-  CK(cudaMemcpyAsync(alpha_dev, a.data(), (size_t)A * sizeof(double), cudaMemcpyHostToDevice, s));
-  CK(fg_coeffs(alpha_dev, (int)A, L, false, coef, nullptr, A, 1, s));
-  const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
-  if (A == 1)
-    CK(fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, coef, (float2*)Q_dev, p->dstatus, s));
-  else
-    CK(fg_assemble_multi(p->c64, p->blk_elems, b0, nb, pb, p->N, (int)A, coef, (float2*)Q_dev, nullptr, p->Np,
-                         p->plane_elems, p->dstatus, s));
+  AssembleWork w = carve_assemble(p, (char*)work, A, L);
+  if (!w.tensor && !p->c64) return FGFRFT_ERR_UNSUPPORTED;
+  CK(cudaMemcpyAsync(w.alpha_dev, a.data(), (size_t)A * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(run_assemble(p, w, w.alpha_dev, A, L, (float2*)Q_dev, nullptr, s));
   return FGFRFT_OK;
 }
 
@@ -480,7 +556,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       return FGFRFT_OK;
     }
     case FGFRFT_PATH_ASSEMBLED: {
-      if (!p->c64 || !fg_tc_available()) return FGFRFT_ERR_UNSUPPORTED;
+      if (!fg_tc_available() || !p->f16 || (!p->c64 && !p->f16T)) return FGFRFT_ERR_UNSUPPORTED;
       std::vector<double> ga((size_t)groups);
       std::vector<int64_t> gstart((size_t)groups), gcount((size_t)groups);
       for (int64_t g = 0; g < groups; ++g) {
@@ -489,9 +565,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
         gcount[(size_t)g] = runs[(size_t)g].second;
       }
       CK(cudaMemcpyAsync(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-      CK(fg_coeffs(w.group_alpha_dev, (int)groups, L, false, w.coef, nullptr, groups, 1, s));
-      CK(fg_assemble_multi(p->c64, p->blk_elems, b0, nb, pb, p->N, (int)groups, w.coef, nullptr, w.Qs, p->Np,
-                           p->plane_elems, p->dstatus, s));
+      CK(run_assemble(p, w.asm_work, w.group_alpha_dev, groups, L, nullptr, w.Qs, s));
       TcGroupedArgs ta{};
       ta.N = p->N;
       ta.Np = p->Np;

@@ -116,135 +116,143 @@ __global__ void __launch_bounds__(K1_THREADS) assemble_single_kernel(const float
 }
 
 // ---------------------------------------------------------------------------
-// K2: A orders in one pass.  Each thread owns EPT complex entries and AC order
-// accumulators per entry; the real coefficients of the powers [nb_pow][AC] and
-// the complex coefficients of P [AC] live in shared memory (broadcast reads).
+// K2: up to 128 orders in one pass over the stack.  The orders form n_og groups of
+// 32; CTA c serves order group c mod n_og, and the n_og CTAs of a group walk the
+// same tile sequence at the same pace, so each stored tile is fetched from HBM once
+// and served to the other CTAs from L2.  Thread t of a CTA accumulates entry t of
+// the 256-entry tile for the 32 orders of its group (64 FP32 accumulators in
+// registers).  Each ring slot holds K2_GB consecutive blocks of the tile (one bulk
+// copy per block), so one barrier round covers K2_GB blocks.  Real coefficients of
+// the powers [nb_pow][32] and the complex coefficients of P live in shared memory and
+// are read as warp-wide broadcasts.
 // ---------------------------------------------------------------------------
-constexpr int K2_THREADS = 256;
-constexpr int K2_STAGES = 8;
+constexpr int K2_CHUNK = 256;
+constexpr int K2_GB = 4;
+constexpr int K2_STAGES = 6;
+constexpr int K2_AC = 32;
 
-template <int AC, int EPT, bool SPLIT>
-__global__ void __launch_bounds__(K2_THREADS) assemble_multi_kernel(
+template <bool SPLIT>
+__global__ void __launch_bounds__(256, 1) assemble_multi_kernel(
     const float2* __restrict__ stack, int64_t blk_elems, int b0, int nb_pow, int p_blk, int64_t N, int A, int a0,
     const float2* __restrict__ coef, float2* __restrict__ Qc, __half* __restrict__ Qs, int64_t Np,
-    int64_t plane_elems, uint32_t* status) {
-  constexpr int CHUNK = K2_THREADS * EPT;
+    int64_t plane_elems, int n_og, uint32_t* status) {
+  constexpr int NT = 256;
+  constexpr int NA = K2_AC;  // orders per CTA
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2* ring = reinterpret_cast<float2*>(smem_raw);            // [STAGES][CHUNK]
-  float2* cpx = ring + K2_STAGES * CHUNK;                        // [AC] complex coefficients of P
-  float* cre = reinterpret_cast<float*>(cpx + AC);               // [nb_pow][AC] real coefficients
-  uint64_t* full = reinterpret_cast<uint64_t*>(cre + (size_t)nb_pow * AC + ((nb_pow * AC) & 1));
+  float2* ring = reinterpret_cast<float2*>(smem_raw);        // [STAGES][GB][CHUNK]
+  float2* cpx = ring + K2_STAGES * K2_GB * K2_CHUNK;         // [NA]
+  float* cre = reinterpret_cast<float*>(cpx + NA);           // [nb_pow][NA]
+  uint64_t* full = reinterpret_cast<uint64_t*>(cre + (size_t)nb_pow * NA);
   const bool has_p = p_blk >= 0;
   const int nblk = nb_pow + (has_p ? 1 : 0);
+  const int ngrp = (nblk + K2_GB - 1) / K2_GB;
   const int tid = threadIdx.x;
-  const int na = (A - a0) < AC ? (A - a0) : AC;
-  for (int t = tid; t < nb_pow * AC; t += K2_THREADS) {
-    const int b = t / AC, a = t % AC;
-    cre[t] = a < na ? coef[(size_t)b * A + a0 + a].x : 0.f;
+  const int e_loc = tid;
+  const int og = (int)(blockIdx.x % n_og);
+  const int cta = (int)(blockIdx.x / n_og), ncta = (int)(gridDim.x / n_og);
+  const int oa0 = a0 + og * K2_AC;  // first order of this CTA
+  const int na = (A - oa0) < NA ? (A - oa0) : NA;
+  for (int t = tid; t < nb_pow * NA; t += NT) {
+    const int b = t / NA, a = t % NA;
+    cre[t] = a < na ? coef[(size_t)b * A + oa0 + a].x : 0.f;
   }
-  for (int a = tid; a < AC; a += K2_THREADS)
-    cpx[a] = (has_p && a < na) ? coef[(size_t)nb_pow * A + a0 + a] : make_float2(0.f, 0.f);
+  for (int a = tid; a < NA; a += NT)
+    cpx[a] = (has_p && a < na) ? coef[(size_t)nb_pow * A + oa0 + a] : make_float2(0.f, 0.f);
   if (tid == 0) {
     for (int s = 0; s < K2_STAGES; ++s) mbar_init(&full[s], 1);
     fence_barrier_init();
   }
   __syncthreads();
   const int64_t NN = N * N;
-  const int64_t ntiles = (NN + CHUNK - 1) / CHUNK;
-  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int64_t items = my_tiles * nblk;
+  const int64_t ntiles = (NN + K2_CHUNK - 1) / K2_CHUNK;
+  const int64_t my_tiles = ntiles > cta ? (ntiles - 1 - cta) / ncta + 1 : 0;
+  const int64_t items = my_tiles * ngrp;
   auto issue = [&](int64_t item) {
     const int s = (int)(item % K2_STAGES);
-    const int64_t t = blockIdx.x + (item / nblk) * gridDim.x;
-    const int b = (int)(item % nblk);
-    const int blk = b < nb_pow ? b0 + b : p_blk;
-    const int64_t e0 = t * CHUNK;
-    const int64_t cnt = (NN - e0) < CHUNK ? (NN - e0) : CHUNK;
+    const int64_t t = cta + (item / ngrp) * ncta;
+    const int g = (int)(item % ngrp);
+    const int64_t e0 = t * K2_CHUNK;
+    const int64_t cnt = (NN - e0) < K2_CHUNK ? (NN - e0) : K2_CHUNK;
     const uint32_t bytes = (uint32_t)(((cnt * 8) + 15) & ~int64_t(15));
-    mbar_arrive_expect_tx(&full[s], bytes);
-    bulk_g2s(ring + (size_t)s * CHUNK, stack + (int64_t)blk * blk_elems + e0, bytes, &full[s]);
+    const int bmax = (nblk - g * K2_GB) < K2_GB ? (nblk - g * K2_GB) : K2_GB;
+    mbar_arrive_expect_tx(&full[s], bytes * (uint32_t)bmax);
+    for (int q = 0; q < bmax; ++q) {
+      const int b = g * K2_GB + q;
+      const int blk = b < nb_pow ? b0 + b : p_blk;
+      bulk_g2s(ring + ((size_t)s * K2_GB + q) * K2_CHUNK, stack + (int64_t)blk * blk_elems + e0, bytes, &full[s]);
+    }
   };
   if (tid == 0) {
     const int64_t pre = items < K2_STAGES ? items : K2_STAGES;
     for (int64_t it = 0; it < pre; ++it) issue(it);
   }
-  float2 acc[EPT][AC];
+  float2 acc[K2_AC];
 #pragma unroll
-  for (int e = 0; e < EPT; ++e)
-#pragma unroll
-    for (int a = 0; a < AC; ++a) acc[e][a] = make_float2(0.f, 0.f);
+  for (int a = 0; a < K2_AC; ++a) acc[a] = make_float2(0.f, 0.f);
   bool ok = true;
   for (int64_t it = 0; it < items; ++it) {
     const int s = (int)(it % K2_STAGES);
     const uint32_t parity = (uint32_t)((it / K2_STAGES) & 1);
-    const int b = (int)(it % nblk);
+    const int g = (int)(it % ngrp);
     if (ok) ok = mbar_wait(&full[s], parity, status);
     if (ok) {
-      float2 x[EPT];
-      if (EPT == 2) {
-        const float4 v = reinterpret_cast<const float4*>(ring + (size_t)s * CHUNK)[tid];
-        x[0] = make_float2(v.x, v.y);
-        x[EPT - 1] = make_float2(v.z, v.w);
-      } else {
-        x[0] = ring[(size_t)s * CHUNK + tid];
-      }
-      if (b < nb_pow) {  // real coefficient: 2 FMAs per entry and order
-        const float4* cb = reinterpret_cast<const float4*>(cre + (size_t)b * AC);
+      const int bmax = (nblk - g * K2_GB) < K2_GB ? (nblk - g * K2_GB) : K2_GB;
+      for (int q = 0; q < bmax; ++q) {
+        const int b = g * K2_GB + q;
+        const float2 x = ring[((size_t)s * K2_GB + q) * K2_CHUNK + e_loc];
+        if (b < nb_pow) {  // real coefficient: 2 FMAs per entry and order
+          const float4* cb = reinterpret_cast<const float4*>(cre + (size_t)b * NA);
 #pragma unroll
-        for (int a4 = 0; a4 < AC / 4; ++a4) {
-          const float4 c = cb[a4];
-          const float cc[4] = {c.x, c.y, c.z, c.w};
+          for (int a4 = 0; a4 < K2_AC / 4; ++a4) {
+            const float4 c = cb[a4];
+            acc[4 * a4 + 0].x = fmaf(c.x, x.x, acc[4 * a4 + 0].x);
+            acc[4 * a4 + 0].y = fmaf(c.x, x.y, acc[4 * a4 + 0].y);
+            acc[4 * a4 + 1].x = fmaf(c.y, x.x, acc[4 * a4 + 1].x);
+            acc[4 * a4 + 1].y = fmaf(c.y, x.y, acc[4 * a4 + 1].y);
+            acc[4 * a4 + 2].x = fmaf(c.z, x.x, acc[4 * a4 + 2].x);
+            acc[4 * a4 + 2].y = fmaf(c.z, x.y, acc[4 * a4 + 2].y);
+            acc[4 * a4 + 3].x = fmaf(c.w, x.x, acc[4 * a4 + 3].x);
+            acc[4 * a4 + 3].y = fmaf(c.w, x.y, acc[4 * a4 + 3].y);
+          }
+        } else {  // the P block: complex coefficient e^{j pi a} (or its derivative)
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-              acc[e][4 * a4 + q].x = fmaf(cc[q], x[e].x, acc[e][4 * a4 + q].x);
-              acc[e][4 * a4 + q].y = fmaf(cc[q], x[e].y, acc[e][4 * a4 + q].y);
-            }
-        }
-      } else {  // the P block: complex coefficient e^{j pi a} (or its derivative)
-#pragma unroll
-        for (int a = 0; a < AC; ++a) {
-          const float2 c = cpx[a];
-#pragma unroll
-          for (int e = 0; e < EPT; ++e) cmac(acc[e][a], c, x[e]);
+          for (int a = 0; a < K2_AC; ++a) cmac(acc[a], cpx[a], x);
         }
       }
     }
-    __syncthreads();
+    __syncthreads();  // every thread is done with slot s
     if (tid == 0 && ok && it + K2_STAGES < items) issue(it + K2_STAGES);
-    if (b == nblk - 1) {
-      const int64_t t = blockIdx.x + (it / nblk) * gridDim.x;
-      const int64_t e = t * CHUNK + (int64_t)EPT * tid;
+    if (g == ngrp - 1) {
+      const int64_t t = cta + (it / ngrp) * ncta;
+      const int64_t e = t * K2_CHUNK + e_loc;
+      if (e < NN) {
+        const int64_t i = e / N, k = e - (e / N) * N;
+        if (!SPLIT) {
+          float2* q = Qc + (int64_t)oa0 * NN + e;
 #pragma unroll
-      for (int ee = 0; ee < EPT; ++ee) {
-        const int64_t g = e + ee;
-        if (g < NN) {
-          const int64_t i = g / N, k = g % N;
+          for (int a = 0; a < K2_AC; ++a) {
+            if (a < na) __stcs(q, acc[a]);
+            q += NN;
+          }
+        } else {
+          const float sc = (float)(1 << FG_SPLIT_SHIFT);
+          __half* q = Qs + (int64_t)oa0 * 4 * plane_elems + i * Np + k;
 #pragma unroll
-          for (int a = 0; a < AC; ++a) {
+          for (int a = 0; a < K2_AC; ++a) {
             if (a < na) {
-              const float2 v = acc[ee][a];
-              if (!SPLIT) {
-                Qc[(int64_t)(a0 + a) * NN + g] = v;
-              } else {
-                const float sc = (float)(1 << FG_SPLIT_SHIFT);
-                const float re = v.x * sc, im = v.y * sc;
-                const __half rh = __float2half_rn(re), ih = __float2half_rn(im);
-                const __half rl = __float2half_rn(re - __half2float(rh));
-                const __half il = __float2half_rn(im - __half2float(ih));
-                __half* base = Qs + (int64_t)(a0 + a) * 4 * plane_elems + i * Np + k;
-                base[0] = rh;
-                base[plane_elems] = rl;
-                base[2 * plane_elems] = ih;
-                base[3 * plane_elems] = il;
-              }
+              const float re = acc[a].x * sc, im = acc[a].y * sc;
+              const __half rh = __float2half_rn(re), ih = __float2half_rn(im);
+              q[0] = rh;
+              q[plane_elems] = __float2half_rn(re - __half2float(rh));
+              q[2 * plane_elems] = ih;
+              q[3 * plane_elems] = __float2half_rn(im - __half2float(ih));
             }
+            q += 4 * plane_elems;
           }
         }
-#pragma unroll
-        for (int a = 0; a < AC; ++a) acc[ee][a] = make_float2(0.f, 0.f);
       }
+#pragma unroll
+      for (int a = 0; a < K2_AC; ++a) acc[a] = make_float2(0.f, 0.f);
     }
   }
   if (!ok && tid == 0) {
@@ -268,27 +276,27 @@ int num_sms() {
   return n;
 }
 
-template <int AC, bool SPLIT>
+template <bool SPLIT>
 cudaError_t launch_multi(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk, int64_t N, int A,
-                         int a0, const float2* coef, float2* Qc, __half* Qs, int64_t Np, int64_t plane_elems,
-                         uint32_t* status, cudaStream_t s) {
-  constexpr int EPT = AC >= 64 ? 1 : 2;
-  constexpr int CHUNK = K2_THREADS * EPT;
-  const size_t smem = (size_t)K2_STAGES * CHUNK * sizeof(float2) + AC * sizeof(float2) +
-                      ((size_t)nb_pow * AC + 1) * sizeof(float) + K2_STAGES * sizeof(uint64_t) + 16;
-  auto kern = assemble_multi_kernel<AC, EPT, SPLIT>;
+                         int a0, int n_og, const float2* coef, float2* Qc, __half* Qs, int64_t Np,
+                         int64_t plane_elems, uint32_t* status, cudaStream_t s) {
+  const size_t smem = (size_t)K2_STAGES * K2_GB * K2_CHUNK * sizeof(float2) + K2_AC * sizeof(float2) +
+                      (size_t)nb_pow * K2_AC * sizeof(float) + K2_STAGES * sizeof(uint64_t) + 16;
+  auto kern = assemble_multi_kernel<SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t NN = N * N;
-  const int64_t ntiles = (NN + CHUNK - 1) / CHUNK;
+  const int64_t ntiles = (NN + K2_CHUNK - 1) / K2_CHUNK;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K2_THREADS, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)num_sms() * per_sm;
-  if (grid > ntiles) grid = ntiles;
-  kern<<<(unsigned)grid, K2_THREADS, smem, s>>>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
-                                                plane_elems, status);
+  int64_t ncta = (int64_t)num_sms() * per_sm / n_og;  // CTAs per order group
+  if (ncta > ntiles) ncta = ntiles;
+  if (ncta < 1) ncta = 1;
+  kern<<<(unsigned)(ncta * n_og), 256, smem, s>>>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
+                                                  plane_elems, n_og, status);
+  fg_note_launch(FGFRFT_KC_ASSEMBLE_MULTI);
   return cudaGetLastError();
 }
 
@@ -309,39 +317,26 @@ cudaError_t fg_assemble_single(const float2* stack, int64_t blk_elems, int b0, i
   const int64_t ntiles = (NN + K1_CHUNK - 1) / K1_CHUNK;
   int64_t grid = (int64_t)num_sms() * per_sm;
   if (grid > ntiles) grid = ntiles;
+  FgTimed timed(FGFRFT_KC_ASSEMBLE_SINGLE, s);
   assemble_single_kernel<<<(unsigned)grid, K1_THREADS, smem, s>>>(stack, blk_elems, b0, nb_pow, p_blk, NN, coef, Q,
                                                                    status);
+  fg_note_launch(FGFRFT_KC_ASSEMBLE_SINGLE);
   return cudaGetLastError();
 }
 
 cudaError_t fg_assemble_multi(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk, int64_t N,
                               int A, const float2* coef, float2* Qc, __half* Qs, int64_t Np, int64_t plane_elems,
                               uint32_t* status, cudaStream_t s) {
-  // orders in passes of at most 64 (one pass over the stack per 64 orders)
-  for (int a0 = 0; a0 < A; a0 += 64) {
-    const int na = (A - a0) < 64 ? (A - a0) : 64;
-    cudaError_t e;
-    const bool split = Qs != nullptr;
-    if (na <= 8)
-      e = split ? launch_multi<8, true>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np, plane_elems,
-                                        status, s)
-                : launch_multi<8, false>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
-                                         plane_elems, status, s);
-    else if (na <= 16)
-      e = split ? launch_multi<16, true>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
-                                         plane_elems, status, s)
-                : launch_multi<16, false>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
-                                          plane_elems, status, s);
-    else if (na <= 32)
-      e = split ? launch_multi<32, true>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
-                                         plane_elems, status, s)
-                : launch_multi<32, false>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
-                                          plane_elems, status, s);
-    else
-      e = split ? launch_multi<64, true>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
-                                         plane_elems, status, s)
-                : launch_multi<64, false>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, coef, Qc, Qs, Np,
-                                          plane_elems, status, s);
+  FgTimed timed(FGFRFT_KC_ASSEMBLE_MULTI, s);
+  // passes of at most 4 order groups of 32 (one pass over the stack per 128 orders)
+  constexpr int kPass = 4 * K2_AC;
+  for (int a0 = 0; a0 < A; a0 += kPass) {
+    const int na = (A - a0) < kPass ? (A - a0) : kPass;
+    const int n_og = (na + K2_AC - 1) / K2_AC;
+    cudaError_t e = Qs != nullptr ? launch_multi<true>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, n_og, coef, Qc,
+                                                       Qs, Np, plane_elems, status, s)
+                                  : launch_multi<false>(stack, blk_elems, b0, nb_pow, p_blk, N, A, a0, n_og, coef, Qc,
+                                                        Qs, Np, plane_elems, status, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

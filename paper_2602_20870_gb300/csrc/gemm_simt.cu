@@ -112,6 +112,8 @@ cudaError_t fg_simt_stacked(const SimtStackArgs& a, cudaStream_t s) {
   if (grid.y > 65535) return cudaErrorInvalidValue;
   const bool scaled = a.coef != nullptr;
   const bool dual = a.D != nullptr;
+  FgTimed timed(FGFRFT_KC_SIMT_GEMM, s);
+  fg_note_launch(FGFRFT_KC_SIMT_GEMM);
   if (!scaled)
     simt_stacked_kernel<false, false><<<grid, 256, 0, s>>>(a);
   else if (!dual)

@@ -65,8 +65,12 @@ struct TcParams {
   int nblk;           // blocks per tile
   int grouped;        // 1: A plane base from the tile, one block; 0: stacked blocks
   int b0, nb_pow, p_blk;
-  int N;
+  int64_t rows;       // rows of A (M extent) and the stride of output columns
   int kchunks;
+  // split output (fused assembly): column j, row r -> Qs[j][plane][r / qN][r % qN] (pitch qNp),
+  // value scaled by 2^FG_SPLIT_SHIFT and split into fp16 hi/lo
+  __half* Qs;
+  int64_t qN, qNp, qplane;
   const float2* coef;
   const float2* coefd;
   int64_t ldcoef;
@@ -289,8 +293,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         sm.scale[et] = ldexpf(1.0f, -(FG_SPLIT_SHIFT + e));
       }
       epi_bar();
-      const int gi = tile.x * TC_BM + row;
-      const bool row_ok = gi < p.N;
+      const int64_t gi = (int64_t)tile.x * TC_BM + row;
+      const bool row_ok = gi < p.rows;
+      int64_t qoff = 0;
+      if (p.Qs) {
+        const int64_t qi = gi / p.qN;
+        qoff = qi * p.qNp + (gi - qi * p.qN);
+      }
       for (int b = 0; b < p.nblk; ++b, ++bc) {
         const uint32_t buf = bc & 1, tph = (bc >> 1) & 1;
         if (!tc_wait(&sm.tfull[buf], tph, sm, p.status)) {
@@ -301,6 +310,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + buf * (2 * TC_BN);
 #pragma unroll 1
         for (int cc = 0; cc < TC_BN / 32; ++cc) {
+          if (tile.z + cc * 32 >= tile.w) break;  // uniform: no column of this chunk is in range
           uint32_t vr[32], vi[32];
           tmem_ld32(base + cc * 32, vr);
           tmem_ld32(base + TC_BN + cc * 32, vi);
@@ -312,8 +322,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (j < tile.w && row_ok) {
               const float sc = sm.scale[jj];
               const float tr = __uint_as_float(vr[c]) * sc, ti = __uint_as_float(vi[c]) * sc;
-              float2* yp = p.Y + (int64_t)j * p.N + gi;
-              if (p.coef == nullptr) {
+              float2* yp = p.Y + (int64_t)j * p.rows + gi;
+              if (p.Qs) {
+                const float sh = (float)(1 << FG_SPLIT_SHIFT);
+                const float re = tr * sh, im = ti * sh;
+                const __half rh = __float2half_rn(re), ih = __float2half_rn(im);
+                __half* q = p.Qs + (int64_t)j * 4 * p.qplane + qoff;
+                q[0] = rh;
+                q[p.qplane] = __float2half_rn(re - __half2float(rh));
+                q[2 * p.qplane] = ih;
+                q[3 * p.qplane] = __float2half_rn(im - __half2float(ih));
+              } else if (p.coef == nullptr) {
                 *yp = make_float2(tr, ti);
               } else {
                 const float2 cf = __ldg(p.coef + (int64_t)b * p.ldcoef + j);
@@ -323,7 +342,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 *yp = y;
                 if (p.D) {
                   const float2 cd = __ldg(p.coefd + (int64_t)b * p.ldcoef + j);
-                  float2* dp = p.D + (int64_t)j * p.N + gi;
+                  float2* dp = p.D + (int64_t)j * p.rows + gi;
                   float2 d = b == 0 ? make_float2(0.f, 0.f) : *dp;
                   d.x = fmaf(cd.x, tr, fmaf(-cd.y, ti, d.x));
                   d.y = fmaf(cd.x, ti, fmaf(cd.y, tr, d.y));
@@ -395,7 +414,7 @@ int sm_count() {
 }
 
 cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vector<int4>& tiles, TcParams p,
-                   void* scratch, size_t scratch_bytes, cudaStream_t s) {
+                   void* scratch, size_t scratch_bytes, cudaStream_t s, int kclass = FGFRFT_KC_TC_GEMM) {
   if (tiles.empty()) return cudaSuccess;
   const size_t tbytes = tiles.size() * sizeof(int4);
   if (tbytes > scratch_bytes) return cudaErrorInvalidValue;
@@ -407,7 +426,9 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vect
   e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = std::min<int>((int)tiles.size(), sm_count());
+  FgTimed timed(kclass, s);
   tc_gemm_kernel<<<grid, TC_THREADS, smem, s>>>(mA, mB, p);
+  fg_note_launch(kclass);
   return cudaGetLastError();
 }
 
@@ -453,7 +474,7 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   TcParams p{};
   p.nblk = 1;
   p.grouped = 1;
-  p.N = (int)a.N;
+  p.rows = a.N;
   p.kchunks = (int)((a.N + TC_KC - 1) / TC_KC);
   p.Y = a.Y;
   p.col_exp = a.col_exp;
@@ -481,7 +502,7 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   p.b0 = a.b0;
   p.nb_pow = a.nb_pow;
   p.p_blk = a.p_blk;
-  p.N = (int)a.N;
+  p.rows = a.N;
   p.kchunks = (int)((a.N + TC_KC - 1) / TC_KC);
   p.coef = a.coef;
   p.coefd = a.coefd;
@@ -491,4 +512,42 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   p.col_exp = a.col_exp;
   p.status = a.status;
   return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s);
+}
+
+cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
+  // Fused multi-order assembly as one complex GEMM: rows = the N*N entries of the
+  // entry-major split stack (K = all stored blocks), columns = the orders, whose
+  // "signals" are their coefficient vectors over the stored blocks.
+  if (a.entries > ((int64_t)1 << 37) || a.A > (1 << 20)) return cudaErrorInvalidValue;
+  cudaError_t e = fg_split_signals(a.coefT, a.A, a.K, a.Kp, a.A, a.Cs, a.col_exp, s);
+  if (e != cudaSuccess) return e;
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, a.entry_stack, a.K, a.entries, a.Kp, 4, a.planeT, TC_BM) ||
+      !make_map(&mB, a.Cs, a.K, a.A, a.Kp, 4, a.A * a.Kp, TC_BN))
+    return cudaErrorInvalidValue;
+  std::vector<int4> tiles;
+  const int64_t row_tiles = (a.entries + TC_BM - 1) / TC_BM;
+  if (row_tiles > INT32_MAX) return cudaErrorInvalidValue;
+  for (int64_t c = 0; c < a.A; c += TC_BN)
+    for (int64_t rt = 0; rt < row_tiles; ++rt)
+      tiles.push_back(make_int4((int)rt, 0, (int)c, (int)std::min<int64_t>(c + TC_BN, a.A)));
+  TcParams p{};
+  p.nblk = 1;
+  p.grouped = 1;
+  p.rows = a.entries;
+  p.kchunks = (int)((a.K + TC_KC - 1) / TC_KC);
+  p.Y = a.Qc;
+  p.Qs = a.Qs;
+  p.qN = a.N;
+  p.qNp = a.Np;
+  p.qplane = a.plane_elems;
+  p.col_exp = a.col_exp;
+  p.status = a.status;
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI);
+}
+
+size_t fg_tc_assemble_scratch_bytes(int64_t entries, int64_t A) {
+  const int64_t row_tiles = (entries + TC_BM - 1) / TC_BM;
+  const int64_t col_tiles = (A + TC_BN - 1) / TC_BN;
+  return (size_t)(row_tiles * col_tiles) * sizeof(int4) + 256;
 }

@@ -22,6 +22,9 @@ struct fgfrft_plan_s {
   uint32_t* dstatus;   // device status word (bit set of kernel error codes)
   float2* c64;         // [nblk][blk_elems] or NULL
   __half* f16;         // [nblk][4][plane_elems] or NULL; planes re_hi, re_lo, im_hi, im_lo
+  __half* f16T;        // entry-major copy [4][N*N][Kp] or NULL (fused multi-order assembly)
+  int64_t Kp;          // entry-major row pitch (nblk rounded up to 8)
+  int64_t planeT;      // entries per entry-major plane (padded to 128)
   int r_neg1;
   double proj_residual;
   int squarings;
@@ -143,6 +146,22 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
 #endif  // __CUDACC__
 
 // ---------------------------------------------------------------------------
+// instrumentation (timing.cu): per-class launch counters and optional event timing
+// ---------------------------------------------------------------------------
+void fg_note_launch(int cls, int n = 1);
+struct FgTimed {  // records a CUDA event pair around its scope when timing is enabled
+  FgTimed(int cls, cudaStream_t s);
+  ~FgTimed();
+  FgTimed(const FgTimed&) = delete;
+  FgTimed& operator=(const FgTimed&) = delete;
+
+ private:
+  int cls_;
+  cudaStream_t s_;
+  long slot_;
+};
+
+// ---------------------------------------------------------------------------
 // launchers (one translation unit each)
 // ---------------------------------------------------------------------------
 // offline.cu
@@ -155,6 +174,8 @@ cudaError_t fg_zmcweeny(int64_t N, const double2* P2, const double2* P3, double2
 cudaError_t fg_ztrace_fro(int64_t N, const double2* S, const double2* Sub, double* out, cudaStream_t s);
 cudaError_t fg_store_block(int64_t N, const double2* M, bool conj_transpose, float2* c64, __half* f16,
                            int64_t Np, int64_t plane_elems, cudaStream_t s);
+cudaError_t fg_entry_major(const __half* f16, int nblk, int64_t N, int64_t Np, int64_t plane_elems, __half* T,
+                           int64_t Kp, int64_t planeT, cudaStream_t s);
 
 // assemble.cu
 cudaError_t fg_assemble_single(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk,
@@ -185,6 +206,10 @@ cudaError_t fg_simt_stacked(const SimtStackArgs& a, cudaStream_t s);
 // coefficient (b, j) at b * ldb + j * ldj; blocks b = 0..2L are the powers -L..L, b = 2L+1 is P
 cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* coef, float2* coefd, int64_t ldb,
                       int64_t ldj, cudaStream_t s);
+// The same coefficients placed at their stored-block positions: power l at L_max + l,
+// P at 2 L_max + 1 (other positions untouched; the caller clears them).
+cudaError_t fg_coeffs_stored(const double* alpha, int B, int L, int L_max, bool adjoint, float2* coef,
+                             int64_t ldb, int64_t ldj, cudaStream_t s);
 int fg_grad_chunks(int64_t N);
 cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N, float* out, double* partials,
                           cudaStream_t s);

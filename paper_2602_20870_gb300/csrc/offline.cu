@@ -218,6 +218,37 @@ __global__ void __launch_bounds__(256) store_block_kernel(int64_t N, const doubl
   }
 }
 
+// Entry-major copy of the split stack: T[p][e][b] = F16[b][p][e / N][e % N] for the
+// stored blocks b < nblk (e = i * N + k).  32 entries x 32 blocks per tile, staged in
+// shared memory so both the reads (along entries) and the writes (along blocks) are
+// contiguous.
+__global__ void __launch_bounds__(256) entry_major_kernel(const __half* __restrict__ f16, int nblk, int64_t N,
+                                                          int64_t Np, int64_t plane_elems, __half* __restrict__ T,
+                                                          int64_t Kp, int64_t planeT) {
+  __shared__ __half tile[32][33];
+  const int64_t e0 = (int64_t)blockIdx.x * 32;
+  const int b0 = blockIdx.y * 32;
+  const int p = blockIdx.z;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t NN = N * N;
+  for (int r = ty; r < 32; r += 8) {  // r: block offset, tx: entry offset
+    const int b = b0 + r;
+    const int64_t e = e0 + tx;
+    __half v = __float2half(0.f);
+    if (b < nblk && e < NN) {
+      const int64_t i = e / N, k = e - (e / N) * N;
+      v = f16[(int64_t)b * 4 * plane_elems + (int64_t)p * plane_elems + i * Np + k];
+    }
+    tile[r][tx] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {  // r: entry offset, tx: block offset
+    const int64_t e = e0 + r;
+    const int b = b0 + tx;
+    if (e < NN && b < Kp) T[(int64_t)p * planeT + e * Kp + b] = tile[tx][r];
+  }
+}
+
 inline int grid_for(int64_t total) {
   int64_t g = (total + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
@@ -238,27 +269,32 @@ cudaError_t fg_zgemm(bool transA, bool transB, int M, int N, int K, double2 alph
     zgemm_kernel<false, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   else
     zgemm_kernel<true, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  fg_note_launch(FGFRFT_KC_OFFLINE);
   return cudaGetLastError();
 }
 
 cudaError_t fg_zaxpby_identity(int64_t N, double2 a, const double2* X, double2 b, double2 d, double2* Y,
                                cudaStream_t s) {
   zaxpby_identity_kernel<<<grid_for(N * N), 256, 0, s>>>(N, a, X, b, d, Y);
+  fg_note_launch(FGFRFT_KC_OFFLINE);
   return cudaGetLastError();
 }
 
 cudaError_t fg_zherm_sym(int64_t N, double2* S, cudaStream_t s) {
   zherm_sym_kernel<<<grid_for(N * N), 256, 0, s>>>(N, S);
+  fg_note_launch(FGFRFT_KC_OFFLINE);
   return cudaGetLastError();
 }
 
 cudaError_t fg_zmcweeny(int64_t N, const double2* P2, const double2* P3, double2* P, cudaStream_t s) {
   zmcweeny_kernel<<<grid_for(N * N), 256, 0, s>>>(N * N, P2, P3, P);
+  fg_note_launch(FGFRFT_KC_OFFLINE);
   return cudaGetLastError();
 }
 
 cudaError_t fg_ztrace_fro(int64_t N, const double2* S, const double2* Sub, double* out, cudaStream_t s) {
   ztrace_fro_kernel<<<1, 1024, 0, s>>>(N, S, Sub, out);
+  fg_note_launch(FGFRFT_KC_OFFLINE);
   return cudaGetLastError();
 }
 
@@ -266,5 +302,15 @@ cudaError_t fg_store_block(int64_t N, const double2* M, bool conj_transpose, flo
                            int64_t plane_elems, cudaStream_t s) {
   dim3 grid((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32));
   store_block_kernel<<<grid, 256, 0, s>>>(N, M, conj_transpose ? 1 : 0, c64, f16, Np, plane_elems);
+  fg_note_launch(FGFRFT_KC_OFFLINE);
+  return cudaGetLastError();
+}
+
+cudaError_t fg_entry_major(const __half* f16, int nblk, int64_t N, int64_t Np, int64_t plane_elems, __half* T,
+                           int64_t Kp, int64_t planeT, cudaStream_t s) {
+  dim3 grid((unsigned)((N * N + 31) / 32), (unsigned)((Kp + 31) / 32), 4);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  entry_major_kernel<<<grid, 256, 0, s>>>(f16, nblk, N, Np, plane_elems, T, Kp, planeT);
+  fg_note_launch(FGFRFT_KC_OFFLINE);
   return cudaGetLastError();
 }

@@ -23,8 +23,10 @@ __device__ double dsinc_series(double u) {
 //   powers: c_l(a) = sin(pi (a - l)) / (pi (a - l)), c_l'(a);  P: e^{j pi a}, j pi e^{j pi a}.
 // sign = -1 evaluates at -a (the adjoint, Prop. 2).
 // Entry (b, j) is stored at b * ldb + j * ldj.
+// Block b is stored at position b + pos_off for the powers and at p_pos for P.
 __global__ void coeffs_kernel(const double* __restrict__ alpha, int B, int L, double sign,
-                              float2* __restrict__ coef, float2* __restrict__ coefd, int64_t ldb, int64_t ldj) {
+                              float2* __restrict__ coef, float2* __restrict__ coefd, int64_t ldb, int64_t ldj,
+                              int pos_off, int p_pos) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (j >= B) return;
@@ -54,8 +56,9 @@ __global__ void coeffs_kernel(const double* __restrict__ alpha, int B, int L, do
     c = make_float2((float)v, 0.f);
     cd = make_float2((float)dv, 0.f);
   }
-  coef[(int64_t)b * ldb + (int64_t)j * ldj] = c;
-  if (coefd) coefd[(int64_t)b * ldb + (int64_t)j * ldj] = cd;
+  const int64_t pos = b == 2 * L + 1 ? p_pos : b + pos_off;
+  coef[pos * ldb + (int64_t)j * ldj] = c;
+  if (coefd) coefd[pos * ldb + (int64_t)j * ldj] = cd;
 }
 
 constexpr int GR_CHUNK = 4096;
@@ -153,7 +156,20 @@ cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* c
                       int64_t ldj, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   dim3 grid((B + 127) / 128, 2 * L + 2);
-  coeffs_kernel<<<grid, 128, 0, s>>>(alpha, B, L, adjoint ? -1.0 : 1.0, coef, coefd, ldb, ldj);
+  FgTimed timed(FGFRFT_KC_COEFFS, s);
+  fg_note_launch(FGFRFT_KC_COEFFS);
+  coeffs_kernel<<<grid, 128, 0, s>>>(alpha, B, L, adjoint ? -1.0 : 1.0, coef, coefd, ldb, ldj, 0, 2 * L + 1);
+  return cudaGetLastError();
+}
+
+cudaError_t fg_coeffs_stored(const double* alpha, int B, int L, int L_max, bool adjoint, float2* coef, int64_t ldb,
+                             int64_t ldj, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  dim3 grid((B + 127) / 128, 2 * L + 2);
+  FgTimed timed(FGFRFT_KC_COEFFS, s);
+  fg_note_launch(FGFRFT_KC_COEFFS);
+  coeffs_kernel<<<grid, 128, 0, s>>>(alpha, B, L, adjoint ? -1.0 : 1.0, coef, nullptr, ldb, ldj, L_max - L,
+                                     2 * L_max + 1);
   return cudaGetLastError();
 }
 
@@ -165,6 +181,8 @@ cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N
   const int nch = fg_grad_chunks(N);
   if (B > 65535) return cudaErrorInvalidValue;
   dim3 grid(nch, (unsigned)B);
+  FgTimed timed(FGFRFT_KC_GRAD_REDUCE, s);
+  fg_note_launch(FGFRFT_KC_GRAD_REDUCE, nch == 1 ? 1 : 2);
   grad_partial_kernel<<<grid, 256, 0, s>>>(G, D, N, nch, partials, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nch == 1) return e;
@@ -175,6 +193,8 @@ cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N
 cudaError_t fg_split_signals(const float2* X, int64_t B, int64_t N, int64_t Np, int64_t rows_pad, __half* planes,
                              int* col_exp, cudaStream_t s) {
   if (rows_pad <= 0) return cudaSuccess;
+  FgTimed timed(FGFRFT_KC_SPLIT_SIGNALS, s);
+  fg_note_launch(FGFRFT_KC_SPLIT_SIGNALS);
   split_signals_kernel<<<(unsigned)rows_pad, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp);
   return cudaGetLastError();
 }

@@ -49,3 +49,25 @@ struct TcStackedArgs {
   uint32_t* status;
 };
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s);
+
+// Fused multi-order assembly on the tensor cores: Q_a = sum_k coefT[a][k] S_k over all
+// stored blocks k (zero coefficients outside -L..L), from the entry-major split stack.
+struct TcAssembleArgs {
+  const __half* entry_stack;  // [4 planes][entries][Kp] fp16 (scaled by 2^FG_SPLIT_SHIFT)
+  int64_t entries;            // N * N
+  int64_t K;                  // stored blocks (2 L_max + 2)
+  int64_t Kp;                 // row pitch of the entry-major planes (K rounded up to 8)
+  int64_t planeT;             // entries per entry-major plane (padded)
+  const float2* coefT;        // [A][K] complex coefficients, order-major
+  int64_t A;
+  __half* Cs;                 // work: [4][A][Kp] split coefficients
+  int* col_exp;               // work: [A]
+  float2* Qc;                 // c64 output [A][N*N] (when Qs is NULL)
+  __half* Qs;                 // split output [A][4][plane_elems] or NULL
+  int64_t N, Np, plane_elems;
+  void* scratch;
+  size_t scratch_bytes;
+  uint32_t* status;
+};
+cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s);
+size_t fg_tc_assemble_scratch_bytes(int64_t entries, int64_t A);

@@ -20,7 +20,7 @@ from .build import LIB
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_NOT_UNITARY, ERR_AMBIGUOUS_SPECTRUM = 1, 2, 3, 4
 ERR_NO_MEMORY, ERR_CUDA, ERR_TIMEOUT = 5, 6, 7
-STORE_C64, STORE_SPLIT_F16 = 1, 2
+STORE_C64, STORE_SPLIT_F16, STORE_ENTRY_F16 = 1, 2, 4
 ADJOINT, SHARED_ALPHA = 1, 2
 PATH_PLAIN, PATH_ASSEMBLED, PATH_STACKED, PATH_STACKED_FP32 = 0x10, 0x20, 0x40, 0x80
 OP_ASSEMBLE, OP_APPLY, OP_GRAD = 1, 2, 3
@@ -47,7 +47,32 @@ SIGNATURES = {
     "fgfrft_assemble": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _sz, _vp]),
     "fgfrft_apply": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp, _sz, _vp]),
     "fgfrft_grad": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp]),
+    "fgfrft_timing_enable": (_i32, [_i32]),
+    "fgfrft_timing_reset": (_i32, []),
+    "fgfrft_timing_read": (_i32, [_i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_dp)]),
 }
+
+# kernel classes (enum fgfrft_kernel_class)
+KERNEL_CLASSES = ["coeffs", "assemble_single", "assemble_multi", "split_signals", "tc_gemm", "simt_gemm",
+                  "grad_reduce", "offline"]
+
+
+def timing_enable(on: bool = True):
+    _check(_lib().fgfrft_timing_enable(1 if on else 0), "fgfrft_timing_enable")
+
+
+def timing_reset():
+    _check(_lib().fgfrft_timing_reset(), "fgfrft_timing_reset")
+
+
+def timing_read() -> dict:
+    """{class: (launches, timed_calls, total_ms)} for every kernel class (synchronises)."""
+    out = {}
+    for i, name in enumerate(KERNEL_CLASSES):
+        n, t, ms = _i64(), _i64(), _dp()
+        _check(_lib().fgfrft_timing_read(i, ctypes.byref(n), ctypes.byref(t), ctypes.byref(ms)), "fgfrft_timing_read")
+        out[name] = (n.value, t.value, ms.value)
+    return out
 
 
 class FGFRFTError(RuntimeError):
@@ -106,7 +131,7 @@ class Plan:
     the device).  The plan's device memory is a torch uint8 tensor owned here.
     """
 
-    def __init__(self, F, L_max: int, storage: int = STORE_C64 | STORE_SPLIT_F16, W=None,
+    def __init__(self, F, L_max: int, storage: int = STORE_C64 | STORE_SPLIT_F16 | STORE_ENTRY_F16, W=None,
                  device="cuda", stream=None):
         lib = _lib()
         Ft = torch.as_tensor(np.asarray(F) if not torch.is_tensor(F) else F)
