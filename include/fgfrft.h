@@ -234,6 +234,32 @@ int fgfrft_timing_enable(int on);
 int fgfrft_timing_reset(void);
 int fgfrft_timing_read(int kernel_class, int64_t* launches, int64_t* timed_calls, double* total_ms);
 
+/*
+ * Zero-allocation alpha-gradient: gradalpha[j] = Re sum_i conj(G_ij) D_ij for
+ * j < B, the same quantity fgfrft_grad returns in gradalpha_dev, for callers that
+ * cannot allocate device memory when they need it (code inside an allocator or
+ * an ordered capture/real-time section where cudaMalloc and cudaFree, which
+ * synchronise the device, are not allowed, or a host that only passes its input
+ * and output buffers).  The paper has no counterpart: this is an interface
+ * choice of the library.
+ *   G_dev, D_dev    B x N c64 (signal j at offset j * N): the output gradient
+ *                   and dY/dalpha from fgfrft_grad's forward.
+ *   gradalpha_dev   B floats, written.
+ * The FP64 partial sums (one per signal and 1024-entry chunk) live in a fixed
+ * array of FGFRFT_NOALLOC_MAX_PARTIALS doubles (512 KiB) in the library's device
+ * memory, which every GPU that loads the library holds until the process exits.
+ * Requests with B * ceil(N / 1024) > FGFRFT_NOALLOC_MAX_PARTIALS return
+ * FGFRFT_ERR_UNSUPPORTED before anything is enqueued.  The call allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library routine.  Its first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and every call overwrites the part it uses, so calls that
+ * overlap on the GPU (different streams without ordering) race.
+ */
+#define FGFRFT_NOALLOC_MAX_PARTIALS 65536
+int fgfrft_grad_alpha_noalloc(const void* G_dev, const void* D_dev, int64_t B, int64_t N,
+                              float* gradalpha_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,7 +50,19 @@ SIGNATURES = {
     "fgfrft_timing_enable": (_i32, [_i32]),
     "fgfrft_timing_reset": (_i32, []),
     "fgfrft_timing_read": (_i32, [_i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_dp)]),
+    "fgfrft_grad_alpha_noalloc": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp]),
 }
+
+NOALLOC_MAX_PARTIALS = 65536
+
+
+def grad_alpha_noalloc(G: torch.Tensor, D: torch.Tensor, out: torch.Tensor, stream=None):
+    """Re <G_j, D_j> per signal row into ``out`` (float32, B) with no device allocation:
+    the library's fixed scratch holds the partial sums (see fgfrft_grad_alpha_noalloc)."""
+    B, N = G.shape
+    rc = _lib().fgfrft_grad_alpha_noalloc(_ptr(G), _ptr(D), B, N, _ptr(out), ctypes.c_void_p(_stream(stream)))
+    _check(rc, "fgfrft_grad_alpha_noalloc")
+    return out
 
 # kernel classes (enum fgfrft_kernel_class)
 KERNEL_CLASSES = ["coeffs", "assemble_single", "assemble_multi", "split_signals", "tc_gemm", "simt_gemm",
