@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="image-graph",
+                    choices=["image-graph", "point-cloud", "precision", "serving"],
+                    help="image-graph is the headline line; the others report the remaining configs")
+    ap.add_argument("--serving-requests", type=int, default=10000)
+    ap.add_argument("--serving-scale", default="full", choices=["full", "small"])
     return ap.parse_args()
 
 
@@ -342,19 +347,30 @@ def run_ours(args):
     k1_bytes = 8.0 * (2 * L + 3) * N * N  # 2L+1 powers + P read, Q written
     k1_gbs = k1_bytes / (ms1 / max(t1, 1) * 1e-3) / 1e9 if t1 else None
 
-    # ---- end to end through the public API from pinned host buffers
+    # ---- end to end through the public API from pinned host buffers: every step copies its
+    # signals to the device and its result back; FG.Pipeline overlaps the copies of one
+    # step with the transform of the next (three streams, double-buffered device tensors)
     Xh = torch.as_tensor(wl.X, dtype=torch.complex64).pin_memory()
     Yh = torch.empty(Xh.shape, dtype=Xh.dtype).pin_memory()
-    for _ in range(2):
-        plan.apply(alpha, Xh, L, out=Yh)
+    pipe = FG.Pipeline(plan, tuple(Xh.shape), L)
+    for _ in range(3):
+        pipe.submit(alpha, Xh, Yh)
+    pipe.wait()
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        plan.apply(alpha, Xh, L, out=Yh)
-        torch.cuda.synchronize()
+        pipe.submit(alpha, Xh, Yh)
+    pipe.wait()
     e2e_s = reduce_max(time.perf_counter() - t0)
     e2e_value = whole_job_rate(n_orders * args.steps, ws, e2e_s)
+    # the same, one synchronous call per step (no overlap between steps)
+    k_serial = max(3, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(k_serial):
+        plan.apply(alpha, Xh, L, out=Yh)
+        torch.cuda.synchronize()
+    e2e_serial = n_orders * k_serial / (time.perf_counter() - t0)
     nbytes = X.numel() * 8
 
     line = {
@@ -375,7 +391,9 @@ def run_ours(args):
                        "simt_gemm_ms_per_step": kt_plain["simt_gemm"][2] / k_plain},
         "roofline": roof,
         "kernels": kernels,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "mode": "pipelined (copies of step k+1 / k-1 overlap the transform of step k)",
+                "serial_value": e2e_serial},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -395,10 +413,175 @@ def run_ours(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- other configs
+def _device_time(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_point_cloud(args):
+    """Differentiation config: Y and dY/dalpha in one pass, then the adjoint and the
+    alpha-gradient (a full forward + backward of the transform), 384 columns."""
+    import torch
+    from paper_2602_20870_gb300 import build as BUILD
+    BUILD.build()
+    from paper_2602_20870_gb300 import fgfrft as FG
+    from paper_2602_20870_gb300 import workloads as W
+    wl = W.point_cloud()
+    N, L, B = wl.N, wl.L, wl.B
+    plan = FG.Plan(wl.F, L)
+    X = torch.as_tensor(wl.X, dtype=torch.complex64).cuda()
+    G = torch.as_tensor(W.complex_normal(wl.X.shape, np.random.default_rng(3)), dtype=torch.complex64).cuda()
+    out = {}
+    for path in ("stacked", "stacked_fp32"):
+        def step():
+            Y, D = plan.forward_dual(wl.alpha, X, L, path=path)
+            plan.backward(wl.alpha, G, D, L, path=path)
+        ms = _device_time(step, args.steps, args.warmup)
+        flops = 3 * 8.0 * (2 * L + 2) * N * N * B  # forward (dual) + adjoint, algorithmic
+        out[path] = {"ms_per_step": ms, "signals_per_s": B / (ms / 1e3), "algorithmic_tflops": flops / ms / 1e9}
+    line = {"metric": "signals/s (forward + dY/dalpha + adjoint + alpha-gradient)", "workload": wl.name,
+            "value": out["stacked"]["signals_per_s"], "unit": "signals/s", "paths": out}
+    if not args.no_cpu_baseline:
+        from oracle import fgfrft_oracle as O
+        cols = np.arange(0, B, 47)
+        Y, D = plan.forward_dual(wl.alpha, X, L, path="stacked")
+        sp = O.spectral(wl.F)
+        P = O.projector(wl.F, sp)
+        t0 = time.perf_counter()
+        Yr = O.apply_power(wl.F, wl.alpha[cols], L, wl.X[cols].T, P).T
+        Dr = O.dalpha_apply(wl.F, wl.alpha[cols], L, wl.X[cols].T, P).T
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(cols) / el, "unit": "signals/s (forward + dual)", "cores": cpu_cores(),
+                                "kind": "oracle", "sample": f"{len(cols)} columns",
+                                "rel_err_Y": _rel(Y.cpu().numpy()[cols], Yr),
+                                "rel_err_D": _rel(D.cpu().numpy()[cols], Dr)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_precision(args):
+    """Precision config (N = 4096, L = 64, 1024 columns): per-column orders on the stacked
+    tensor-core path, one shared order on the assembled tensor path and on the plain FP32
+    path, each with its error against the FP64 oracle on sampled columns."""
+    import torch
+    from paper_2602_20870_gb300 import build as BUILD
+    BUILD.build()
+    from paper_2602_20870_gb300 import fgfrft as FG
+    from paper_2602_20870_gb300 import workloads as W
+    wl = W.precision()
+    N, L, B = wl.N, wl.L, wl.B
+    t0 = time.perf_counter()
+    plan = FG.Plan(wl.F, L)
+    offline_s = time.perf_counter() - t0
+    X = torch.as_tensor(wl.X, dtype=torch.complex64).cuda()
+    res = {}
+    outs = {}
+    cases = [("stacked", wl.alpha, "stacked"), ("assembled_shared", np.full(B, 0.37), "assembled"),
+             ("plain_shared", np.full(B, 0.37), "plain")]
+    for name, a, path in cases:
+        ms = _device_time(lambda: plan.apply(a, X, L, path=path), max(2, args.steps // 4), 2)
+        outs[name] = plan.apply(a, X, L, path=path).cpu().numpy()
+        res[name] = {"ms": ms, "signals_per_s": B / (ms / 1e3)}
+    # single-order assembly at this size (17.6 GB streamed per order)
+    FG.timing_reset()
+    FG.timing_enable(True)
+    ms1 = _device_time(lambda: plan.assemble([0.37], L), 5, 2)
+    FG.timing_enable(False)
+    n1, t1, k1 = FG.timing_read()["assemble_single"]
+    byts = 8.0 * (2 * L + 3) * N * N
+    peaks, src = measured_peaks()
+    res["assemble_single"] = {"ms": k1 / max(t1, 1), "order_updates_per_s": 1e3 / (k1 / max(t1, 1)),
+                              "achieved_gbs": byts / (k1 / max(t1, 1) * 1e-3) / 1e9,
+                              "frac_of_hbm": byts / (k1 / max(t1, 1) * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+    line = {"metric": "signals/s and order-updates/s", "workload": wl.name, "unit": "signals/s",
+            "value": res["stacked"]["signals_per_s"], "paths": res, "offline_precompute_s": offline_s}
+    if not args.no_cpu_baseline:
+        from oracle import fgfrft_oracle as O
+        import scipy.linalg
+        lam = scipy.linalg.eigvals(wl.F.real)
+        P = np.zeros((N, N), complex) if np.min(np.abs(lam + 1)) > 1e-6 else O.projector(wl.F)
+        cols = np.arange(0, B, 128)
+        t0 = time.perf_counter()
+        refs = {"stacked": O.apply_power(wl.F, wl.alpha[cols], L, wl.X[cols].T, P).T}
+        el = time.perf_counter() - t0
+        refs["assembled_shared"] = refs["plain_shared"] = O.apply_power(wl.F, 0.37, L, wl.X[cols].T, P).T
+        line["cpu_baseline"] = {"value": len(cols) / el, "unit": "signals/s", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": f"{len(cols)} columns (signal recursion, no stored powers)"}
+        line["rel_err_vs_fp64"] = {k: _rel(outs[k][cols], refs[k]) for k in refs}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args):
+    """Serving config: Poisson arrivals over 8 resident graphs, continuous batching against
+    the plain one-request-at-a-time FP32 path, at 0.3 .. 1.2 x the sequential capacity."""
+    import torch
+    from paper_2602_20870_gb300 import build as BUILD
+    BUILD.build()
+    from paper_2602_20870_gb300 import fgfrft as FG
+    from paper_2602_20870_gb300 import serving as S
+    from paper_2602_20870_gb300 import workloads as W
+    sizes = [256, 512, 1024, 1024, 2048, 2048, 4096, 4096] if args.serving_scale == "full" else \
+        [64, 128, 256, 256, 512, 512, 1024, 1024]
+    L_max = 64 if args.serving_scale == "full" else 32
+    Ls = (16, 32, 64) if L_max == 64 else (8, 16, 32)
+    t0 = time.perf_counter()
+    plans = [FG.Plan(W.rgg_gft(n, 500 + i), L_max) for i, n in enumerate(sizes)]
+    offline_s = time.perf_counter() - t0
+    resident = sum(p.plan_bytes for p in plans)
+    budget = 150 * 2 ** 30
+    # sequential capacity from a sample run back to back
+    sample = W.serving_requests(sizes, 200, rate_per_s=1e9, seed=55, Ls=Ls, lazy=True)
+    S.sequential(plans, sample[:20], time_scale=0.0)
+    t0 = time.perf_counter()
+    S.sequential(plans, sample, time_scale=0.0)
+    capacity = len(sample) / (time.perf_counter() - t0)
+    sweep = []
+    for frac in (0.3, 0.6, 0.9, 1.2):
+        reqs = W.serving_requests(sizes, args.serving_requests, rate_per_s=frac * capacity, seed=5, Ls=Ls, lazy=True)
+        srv = S.Server(plans, budget - resident, max_cols=512, max_inflight_per_graph=2)
+        t0 = time.perf_counter()
+        res = S.replay(srv, reqs, timeout_s=3600)
+        torch.cuda.synchronize()
+        span = time.perf_counter() - t0
+        seq = S.sequential(plans, reqs)
+        seq_span = max(r.done for r in seq)
+        sweep.append({"rate_frac_of_capacity": frac, "rate_per_s": frac * capacity,
+                      "batched": {**S.latency_stats(res), "throughput_rps": len(reqs) / span,
+                                  "launches": srv.launches, "max_reserved_gb": srv.max_reserved / 2 ** 30},
+                      "sequential_plain": {**S.latency_stats(seq), "throughput_rps": len(reqs) / seq_span}})
+    line = {"metric": "serving p50/p99 latency and throughput vs plain sequential FP32", "unit": "requests/s",
+            "value": sweep[-1]["batched"]["throughput_rps"], "graphs": sizes, "L_max": L_max,
+            "requests_per_point": args.serving_requests, "sequential_capacity_rps": capacity,
+            "resident_plan_gb": resident / 2 ** 30, "offline_precompute_s": offline_s, "sweep": sweep}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "point-cloud":
+        return run_point_cloud(args)
+    if args.workload == "precision":
+        return run_precision(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

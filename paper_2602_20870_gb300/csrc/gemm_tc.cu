@@ -11,12 +11,13 @@
 //   acc_re += Ar*Xr - Ai*Xi ,  acc_im += Ar*Xi + Ai*Xr   (3 split products each term)
 // with FP32 accumulation in tensor memory (TMEM).
 //
-// CTA layout (192 threads, one CTA per SM, persistent over a tile list):
+// CTA layout (320 threads, one CTA per SM, persistent over a tile list):
 //   warp 0      TMA producer: 3-D tensor-map loads of 4 A planes + 4 X planes per
 //               stage (32 k-values, 64-byte swizzled rows) into a 3-stage ring;
 //   warp 1      allocates 512 TMEM columns; one thread issues tcgen05.mma and
 //               tcgen05.commit; accumulators double-buffered (2 x [re 128 | im 128]);
-//   warps 2..5  epilogue: tcgen05.ld the finished block, undo the power-of-two
+//   warps 2..9  epilogue (two warps per TMEM lane quadrant, alternate 32-column
+//               chunks): tcgen05.ld the finished block, undo the power-of-two
 //               scales, apply the per-column coefficients, and accumulate into Y/D in
 //               global memory (each output tile is owned by one CTA, blocks in order,
 //               so the sums are deterministic).
@@ -33,31 +34,37 @@
 namespace {
 
 constexpr int TC_BM = 128;                 // rows per tile (TMEM lanes)
-constexpr int TC_BN = 128;                 // complex columns per tile
 constexpr int TC_KC = 32;                  // k per stage: 32 fp16 = 64-byte rows
-constexpr int TC_STAGES = 3;
 constexpr int TC_PLANE_A = TC_BM * TC_KC * 2;  // 8 KB
-constexpr int TC_PLANE_B = TC_BN * TC_KC * 2;  // 8 KB
-constexpr int TC_STAGE_BYTES = 4 * TC_PLANE_A + 4 * TC_PLANE_B;
-constexpr int TC_TMEM_COLS = 512;
-constexpr int TC_THREADS = 192;
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // producer warp, MMA warp, epilogue warps
 constexpr int TC_EPI_WARP0 = 2;
+constexpr int TC_BN_MAX = 128;
 
+// Column-tile width BN (complex columns per tile): 128, or 64 for few columns.
+template <int BN>
+struct TcCfg {
+  static constexpr int PLANE_B = BN * TC_KC * 2;
+  static constexpr int STAGE_BYTES = 4 * TC_PLANE_A + 4 * PLANE_B;
+  static constexpr int STAGES = BN == 128 ? 3 : 4;
+  static constexpr int TMEM_COLS = 4 * BN;  // 2 buffers x [re BN | im BN]
+  // kind::f16 instruction descriptor: D f32, A/B f16, both K-major, N = BN, M = 128.
+  static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+  static constexpr uint32_t IDESC_NEG_A = IDESC | (1u << 13);
+};
+
+template <int BN>
 struct __align__(1024) TcSmem {
-  uint8_t stage[TC_STAGES][TC_STAGE_BYTES];
-  uint64_t full[TC_STAGES];
-  uint64_t empty[TC_STAGES];
+  uint8_t stage[TcCfg<BN>::STAGES][TcCfg<BN>::STAGE_BYTES];
+  uint64_t full[TcCfg<BN>::STAGES];
+  uint64_t empty[TcCfg<BN>::STAGES];
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t drain;
   uint32_t tmem_base;
   volatile int abort;
-  float scale[TC_BN];
+  float scale[BN];
 };
-
-// kind::f16 instruction descriptor: D f32, A/B f16, both K-major, N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-constexpr uint32_t kIdescNegA = kIdesc | (1u << 13);
 
 struct TcParams {
   const int4* tiles;  // {row tile, A plane base (grouped), first column, end column}
@@ -129,7 +136,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Bounded wait that also gives up at once when another role already aborted.
-__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, TcSmem& sm, uint32_t* status) {
+template <class Smem>
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, Smem& sm, uint32_t* status) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   while (true) {
@@ -143,12 +151,22 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, TcSmem& 
   }
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory"); }
 
+template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+  using Cfg = TcCfg<BN>;
+  constexpr int TC_STAGES = Cfg::STAGES;
+  constexpr int TC_BN = BN;
+  constexpr int TC_PLANE_B = Cfg::PLANE_B;
+  constexpr int TC_STAGE_BYTES = Cfg::STAGE_BYTES;
+  constexpr int TC_TMEM_COLS = Cfg::TMEM_COLS;
+  constexpr uint32_t kIdesc = Cfg::IDESC;
+  constexpr uint32_t kIdescNegA = Cfg::IDESC_NEG_A;
   extern __shared__ uint8_t smem_raw[];
-  TcSmem& sm = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TcSmem<BN>& sm =
+      *reinterpret_cast<TcSmem<BN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
@@ -159,7 +177,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm.tfull[b], 1);
-      mbar_init(&sm.tempty[b], 4);
+      mbar_init(&sm.tempty[b], TC_EPI_WARPS);
     }
     mbar_init(&sm.drain, 1);
     sm.abort = 0;
@@ -182,10 +200,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       uint32_t kit = 0;
-      uint32_t issued[TC_STAGES] = {0, 0, 0};
+      uint32_t issued[TC_STAGES] = {};
       bool ok = true;
+      int4 next = blockIdx.x < p.ntiles ? p.tiles[blockIdx.x] : make_int4(0, 0, 0, 0);
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
-        const int4 tile = p.tiles[t];
+        const int4 tile = next;
+        if (t + (int)gridDim.x < p.ntiles) next = p.tiles[t + gridDim.x];  // prefetch
         for (int b = 0; ok && b < p.nblk; ++b) {
           const int zA = p.grouped ? tile.y : 4 * (b < p.nb_pow ? p.b0 + b : p.p_blk);
           for (int kc = 0; kc < p.kchunks; ++kc, ++kit) {
@@ -279,24 +299,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // 8 warps: warps w and w+4 read the same TMEM lane quadrant (w mod 4) and take
+    // alternate 32-column chunks of the tile.
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const int half = (warp - TC_EPI_WARP0) >> 2;
     const int row = 32 * q + lane;
-    const int et = threadIdx.x - TC_EPI_WARP0 * 32;  // 0..127
+    const int et = threadIdx.x - TC_EPI_WARP0 * 32;  // 0..255
+    const bool split_out = p.Qs != nullptr;
     uint32_t bc = 0;
     bool ok = true;
+    // one scale per column: undo 2^{e_j} and the operator scale; the next tile's
+    // descriptor and scales are loaded while the current tile is processed
+    auto col_scale = [&](const int4& tl) -> float {
+      if (et >= TC_BN) return 0.f;
+      const int j = tl.z + et;
+      const int e = j < tl.w ? p.col_exp[j] : 0;
+      return ldexpf(1.0f, split_out ? -e : -(FG_SPLIT_SHIFT + e));
+    };
+    int4 next = blockIdx.x < p.ntiles ? p.tiles[blockIdx.x] : make_int4(0, 0, 0, 0);
+    float next_scale = blockIdx.x < p.ntiles ? col_scale(next) : 0.f;
     for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
-      const int4 tile = p.tiles[t];
-      epi_bar();
-      {
-        const int j = tile.z + et;
-        const int e = j < tile.w ? p.col_exp[j] : 0;
-        sm.scale[et] = ldexpf(1.0f, -(FG_SPLIT_SHIFT + e));
+      const int4 tile = next;
+      const float my_scale = next_scale;
+      if (t + (int)gridDim.x < p.ntiles) {
+        next = p.tiles[t + gridDim.x];
+        next_scale = col_scale(next);
       }
+      epi_bar();
+      if (et < TC_BN) sm.scale[et] = my_scale;
       epi_bar();
       const int64_t gi = (int64_t)tile.x * TC_BM + row;
       const bool row_ok = gi < p.rows;
       int64_t qoff = 0;
-      if (p.Qs) {
+      if (split_out) {
         const int64_t qi = gi / p.qN;
         qoff = qi * p.qNp + (gi - qi * p.qN);
       }
@@ -309,46 +344,71 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         fence_tc_after();
         const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + buf * (2 * TC_BN);
 #pragma unroll 1
-        for (int cc = 0; cc < TC_BN / 32; ++cc) {
-          if (tile.z + cc * 32 >= tile.w) break;  // uniform: no column of this chunk is in range
+        for (int cc = half; cc < TC_BN / 32; cc += 2) {
+          const int j0 = tile.z + cc * 32;
+          if (j0 >= tile.w) break;  // uniform: no column of this chunk is in range
+          const int ncol = min(32, tile.w - j0);
           uint32_t vr[32], vi[32];
+          __syncwarp();  // tcgen05.ld is warp-collective: the whole warp converged
           tmem_ld32(base + cc * 32, vr);
           tmem_ld32(base + TC_BN + cc * 32, vi);
           tmem_wait_ld();
+          if (!row_ok) {
+            // rows past the end: nothing to store
+          } else if (split_out) {
+            // value * 2^FG_SPLIT_SHIFT as fp16 hi + lo, four planes per column
+            const int64_t pl = p.qplane;
+            __half* qp = p.Qs + (int64_t)j0 * 4 * pl + qoff;
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            const int jj = cc * 32 + c;
-            const int j = tile.z + jj;
-            if (j < tile.w && row_ok) {
-              const float sc = sm.scale[jj];
-              const float tr = __uint_as_float(vr[c]) * sc, ti = __uint_as_float(vi[c]) * sc;
-              float2* yp = p.Y + (int64_t)j * p.rows + gi;
-              if (p.Qs) {
-                const float sh = (float)(1 << FG_SPLIT_SHIFT);
-                const float re = tr * sh, im = ti * sh;
-                const __half rh = __float2half_rn(re), ih = __float2half_rn(im);
-                __half* q = p.Qs + (int64_t)j * 4 * p.qplane + qoff;
-                q[0] = rh;
-                q[p.qplane] = __float2half_rn(re - __half2float(rh));
-                q[2 * p.qplane] = ih;
-                q[3 * p.qplane] = __float2half_rn(im - __half2float(ih));
-              } else if (p.coef == nullptr) {
-                *yp = make_float2(tr, ti);
-              } else {
-                const float2 cf = __ldg(p.coef + (int64_t)b * p.ldcoef + j);
+            for (int c = 0; c < 32; ++c) {
+              if (c < ncol) {
+                const float sc = sm.scale[cc * 32 + c];
+                const float re = __uint_as_float(vr[c]) * sc, im = __uint_as_float(vi[c]) * sc;
+                const __half2 hi = __floats2half2_rn(re, im);
+                const float2 hf = __half22float2(hi);
+                const __half2 lo = __floats2half2_rn(re - hf.x, im - hf.y);
+                qp[0] = __low2half(hi);
+                qp[pl] = __low2half(lo);
+                qp[2 * pl] = __high2half(hi);
+                qp[3 * pl] = __high2half(lo);
+              }
+              qp += 4 * pl;
+            }
+          } else if (p.coef == nullptr) {
+            float2* yp = p.Y + (int64_t)j0 * p.rows + gi;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              if (c < ncol) {
+                const float sc = sm.scale[cc * 32 + c];
+                *yp = make_float2(__uint_as_float(vr[c]) * sc, __uint_as_float(vi[c]) * sc);
+              }
+              yp += p.rows;
+            }
+          } else {
+            float2* yp = p.Y + (int64_t)j0 * p.rows + gi;
+            float2* dp = p.D ? p.D + (int64_t)j0 * p.rows + gi : nullptr;
+            const float2* cfp = p.coef + (int64_t)b * p.ldcoef + j0;
+            const float2* cdp = p.D ? p.coefd + (int64_t)b * p.ldcoef + j0 : nullptr;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              if (c < ncol) {
+                const float sc = sm.scale[cc * 32 + c];
+                const float tr = __uint_as_float(vr[c]) * sc, ti = __uint_as_float(vi[c]) * sc;
+                const float2 cf = __ldg(cfp + c);
                 float2 y = b == 0 ? make_float2(0.f, 0.f) : *yp;
                 y.x = fmaf(cf.x, tr, fmaf(-cf.y, ti, y.x));
                 y.y = fmaf(cf.x, ti, fmaf(cf.y, tr, y.y));
                 *yp = y;
-                if (p.D) {
-                  const float2 cd = __ldg(p.coefd + (int64_t)b * p.ldcoef + j);
-                  float2* dp = p.D + (int64_t)j * p.rows + gi;
+                if (dp) {
+                  const float2 cd = __ldg(cdp + c);
                   float2 d = b == 0 ? make_float2(0.f, 0.f) : *dp;
                   d.x = fmaf(cd.x, tr, fmaf(-cd.y, ti, d.x));
                   d.y = fmaf(cd.x, ti, fmaf(cd.y, tr, d.y));
                   *dp = d;
                 }
               }
+              yp += p.rows;
+              if (dp) dp += p.rows;
             }
           }
         }
@@ -413,8 +473,23 @@ int sm_count() {
   return n;
 }
 
+template <int BN>
+cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, int ntiles, const TcParams& p, cudaStream_t s,
+                      int kclass) {
+  const size_t smem = sizeof(TcSmem<BN>) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min<int>(ntiles, sm_count());
+  FgTimed timed(kclass, s);
+  tc_gemm_kernel<BN><<<grid, TC_THREADS, smem, s>>>(mA, mB, p);
+  fg_note_launch(kclass);
+  return cudaGetLastError();
+}
+
+// bn: column-tile width (64 or 128); the B tensor map's box must have bn rows.
 cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vector<int4>& tiles, TcParams p,
-                   void* scratch, size_t scratch_bytes, cudaStream_t s, int kclass = FGFRFT_KC_TC_GEMM) {
+                   void* scratch, size_t scratch_bytes, cudaStream_t s, int kclass = FGFRFT_KC_TC_GEMM,
+                   int bn = 128) {
   if (tiles.empty()) return cudaSuccess;
   const size_t tbytes = tiles.size() * sizeof(int4);
   if (tbytes > scratch_bytes) return cudaErrorInvalidValue;
@@ -422,14 +497,7 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vect
   if (e != cudaSuccess) return e;
   p.tiles = (const int4*)scratch;
   p.ntiles = (int)tiles.size();
-  const size_t smem = sizeof(TcSmem) + 1024;
-  e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int grid = std::min<int>((int)tiles.size(), sm_count());
-  FgTimed timed(kclass, s);
-  tc_gemm_kernel<<<grid, TC_THREADS, smem, s>>>(mA, mB, p);
-  fg_note_launch(kclass);
-  return cudaGetLastError();
+  return bn == 64 ? launch_bn<64>(mA, mB, p.ntiles, p, s, kclass) : launch_bn<128>(mA, mB, p.ntiles, p, s, kclass);
 }
 
 }  // namespace
@@ -451,7 +519,7 @@ int64_t fg_tc_signal_rows(int64_t B, int64_t) { return B; }
 
 size_t fg_tc_scratch_bytes(int64_t N, int64_t B, int64_t groups, int) {
   const int64_t row_tiles = (N + TC_BM - 1) / TC_BM;
-  const int64_t col_tiles = (B + TC_BN - 1) / TC_BN + groups;  // each group may add a ragged tile
+  const int64_t col_tiles = (B + 63) / 64 + groups;  // each group may add a ragged tile (tiles >= 64 wide)
   return (size_t)(row_tiles * col_tiles) * sizeof(int4) + 256;
 }
 
@@ -461,15 +529,15 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
   if (!make_map(&mA, a.Qs, a.N, a.N, a.Np, 4 * a.groups, a.plane_elems, TC_BM) ||
-      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN))
+      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN_MAX))
     return cudaErrorInvalidValue;
   std::vector<int4> tiles;
   const int row_tiles = (int)((a.N + TC_BM - 1) / TC_BM);
   for (int64_t g = 0; g < a.groups; ++g) {
     const int64_t c0 = a.gstart[g], c1 = a.gstart[g] + a.gcount[g];
     for (int rt = 0; rt < row_tiles; ++rt)
-      for (int64_t c = c0; c < c1; c += TC_BN)
-        tiles.push_back(make_int4(rt, (int)(4 * g), (int)c, (int)std::min<int64_t>(c + TC_BN, c1)));
+      for (int64_t c = c0; c < c1; c += TC_BN_MAX)
+        tiles.push_back(make_int4(rt, (int)(4 * g), (int)c, (int)std::min<int64_t>(c + TC_BN_MAX, c1)));
   }
   TcParams p{};
   p.nblk = 1;
@@ -489,13 +557,13 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   CUtensorMap mA, mB;
   const int64_t nplanes = 4 * (int64_t)(std::max(a.b0 + a.nb_pow, a.p_blk + 1));
   if (!make_map(&mA, a.stack, a.N, a.N, a.Np, nplanes, a.plane_elems, TC_BM) ||
-      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN))
+      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN_MAX))
     return cudaErrorInvalidValue;
   std::vector<int4> tiles;
   const int row_tiles = (int)((a.N + TC_BM - 1) / TC_BM);
   for (int rt = 0; rt < row_tiles; ++rt)
-    for (int64_t c = 0; c < a.B; c += TC_BN)
-      tiles.push_back(make_int4(rt, 0, (int)c, (int)std::min<int64_t>(c + TC_BN, a.B)));
+    for (int64_t c = 0; c < a.B; c += TC_BN_MAX)
+      tiles.push_back(make_int4(rt, 0, (int)c, (int)std::min<int64_t>(c + TC_BN_MAX, a.B)));
   TcParams p{};
   p.nblk = a.nb_pow + (a.p_blk >= 0 ? 1 : 0);
   p.grouped = 0;
@@ -521,16 +589,17 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   if (a.entries > ((int64_t)1 << 37) || a.A > (1 << 20)) return cudaErrorInvalidValue;
   cudaError_t e = fg_split_signals(a.coefT, a.A, a.K, a.Kp, a.A, a.Cs, a.col_exp, s);
   if (e != cudaSuccess) return e;
+  const int bn = a.A <= 64 ? 64 : 128;
   CUtensorMap mA, mB;
   if (!make_map(&mA, a.entry_stack, a.K, a.entries, a.Kp, 4, a.planeT, TC_BM) ||
-      !make_map(&mB, a.Cs, a.K, a.A, a.Kp, 4, a.A * a.Kp, TC_BN))
+      !make_map(&mB, a.Cs, a.K, a.A, a.Kp, 4, a.A * a.Kp, bn))
     return cudaErrorInvalidValue;
   std::vector<int4> tiles;
   const int64_t row_tiles = (a.entries + TC_BM - 1) / TC_BM;
   if (row_tiles > INT32_MAX) return cudaErrorInvalidValue;
-  for (int64_t c = 0; c < a.A; c += TC_BN)
+  for (int64_t c = 0; c < a.A; c += bn)
     for (int64_t rt = 0; rt < row_tiles; ++rt)
-      tiles.push_back(make_int4((int)rt, 0, (int)c, (int)std::min<int64_t>(c + TC_BN, a.A)));
+      tiles.push_back(make_int4((int)rt, 0, (int)c, (int)std::min<int64_t>(c + bn, a.A)));
   TcParams p{};
   p.nblk = 1;
   p.grouped = 1;
@@ -543,11 +612,11 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   p.qplane = a.plane_elems;
   p.col_exp = a.col_exp;
   p.status = a.status;
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI);
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, bn);
 }
 
 size_t fg_tc_assemble_scratch_bytes(int64_t entries, int64_t A) {
   const int64_t row_tiles = (entries + TC_BM - 1) / TC_BM;
-  const int64_t col_tiles = (A + TC_BN - 1) / TC_BN;
+  const int64_t col_tiles = (A + 63) / 64;
   return (size_t)(row_tiles * col_tiles) * sizeof(int4) + 256;
 }

@@ -102,6 +102,8 @@ __global__ void grad_final_kernel(const double* __restrict__ partial, int nchunk
 
 // One CTA per signal column j: e_j such that max(|re|, |im|) * 2^e_j lies in
 // [2^13, 2^14); planes[p][j][k] for p = re_hi, re_lo, im_hi, im_lo of x * 2^e_j.
+// Each thread handles 4 consecutive entries per round (8-byte plane stores); entries
+// k in [N, Np) are written as zeros.
 __global__ void __launch_bounds__(256) split_signals_kernel(const float2* __restrict__ X, int64_t B, int64_t N,
                                                             int64_t Np, int64_t rows_pad, __half* __restrict__ planes,
                                                             int* __restrict__ col_exp) {
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const float2* __rest
   __half* r_lo = r_hi + plane;
   __half* i_hi = r_hi + 2 * plane;
   __half* i_lo = r_hi + 3 * plane;
+  const float2* x = X + j * N;
   if (j >= B) {  // padding rows are zero
     for (int64_t k = threadIdx.x; k < Np; k += blockDim.x) {
       r_hi[k] = r_lo[k] = i_hi[k] = i_lo[k] = __float2half(0.f);
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const float2* __rest
   }
   float m = 0.f;
   for (int64_t k = threadIdx.x; k < N; k += blockDim.x) {
-    const float2 v = X[j * N + k];
+    const float2 v = x[k];
     m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
   }
   __shared__ float red[8];
@@ -135,18 +138,30 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const float2* __rest
     e = (FG_X_TARGET_EXP + 1) - E;
   }
   if (threadIdx.x == 0) col_exp[j] = e;
-  for (int64_t k = threadIdx.x; k < Np; k += blockDim.x) {
-    float re = 0.f, im = 0.f;
-    if (k < N) {
-      const float2 v = X[j * N + k];
-      re = ldexpf(v.x, e);
-      im = ldexpf(v.y, e);
+  // Np is a multiple of 8, so groups of 4 entries never straddle the row end
+  for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < Np; k0 += 4 * (int64_t)blockDim.x) {
+    __align__(8) __half rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = k0 + u;
+      float re = 0.f, im = 0.f;
+      if (k < N) {
+        const float2 v = x[k];
+        re = ldexpf(v.x, e);
+        im = ldexpf(v.y, e);
+      }
+      const __half2 hi = __floats2half2_rn(re, im);
+      const float2 hf = __half22float2(hi);
+      const __half2 lo = __floats2half2_rn(re - hf.x, im - hf.y);
+      rh[u] = __low2half(hi);
+      ih[u] = __high2half(hi);
+      rl[u] = __low2half(lo);
+      il[u] = __high2half(lo);
     }
-    const __half rh = __float2half_rn(re), ih = __float2half_rn(im);
-    r_hi[k] = rh;
-    r_lo[k] = __float2half_rn(re - __half2float(rh));
-    i_hi[k] = ih;
-    i_lo[k] = __float2half_rn(im - __half2float(ih));
+    *reinterpret_cast<uint2*>(r_hi + k0) = *reinterpret_cast<const uint2*>(rh);
+    *reinterpret_cast<uint2*>(r_lo + k0) = *reinterpret_cast<const uint2*>(rl);
+    *reinterpret_cast<uint2*>(i_hi + k0) = *reinterpret_cast<const uint2*>(ih);
+    *reinterpret_cast<uint2*>(i_lo + k0) = *reinterpret_cast<const uint2*>(il);
   }
 }
 

@@ -291,6 +291,46 @@ class Plan:
         return gX, ga
 
 
+class Pipeline:
+    """Streams host batches through ``Plan.apply``: the copy of batch k+1 to the device,
+    the transform of batch k and the copy of batch k-1 back to the host run on three
+    CUDA streams at once, with two device buffers per side.  ``submit`` returns at once;
+    ``wait`` blocks until every submitted batch is back in its host buffer."""
+
+    def __init__(self, plan: Plan, shape, L: int | None = None, path: str = "auto"):
+        self.plan, self.L, self.path = plan, plan.L_max if L is None else int(L), path
+        dev = plan.device
+        self.s_in, self.s_run, self.s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        self.X = [torch.empty(shape, dtype=torch.complex64, device=dev) for _ in range(2)]
+        self.Y = [torch.empty(shape, dtype=torch.complex64, device=dev) for _ in range(2)]
+        self.ev_in = [torch.cuda.Event() for _ in range(2)]
+        self.ev_run = [torch.cuda.Event() for _ in range(2)]
+        self.ev_out = [torch.cuda.Event() for _ in range(2)]
+        self.k = 0
+
+    def submit(self, alpha, Xh: torch.Tensor, Yh: torch.Tensor):
+        """Enqueue Yh = Q X for pinned host tensors Xh, Yh."""
+        b = self.k % 2
+        if self.k >= 2:
+            self.s_in.wait_event(self.ev_run[b])    # X[b] no longer read by batch k-2
+            self.s_run.wait_event(self.ev_out[b])   # Y[b] already copied out
+        with torch.cuda.stream(self.s_in):
+            self.X[b].copy_(Xh, non_blocking=True)
+            self.ev_in[b].record(self.s_in)
+        self.s_run.wait_event(self.ev_in[b])
+        with torch.cuda.stream(self.s_run):
+            self.plan.apply(alpha, self.X[b], self.L, path=self.path, out=self.Y[b], stream=self.s_run)
+            self.ev_run[b].record(self.s_run)
+        self.s_out.wait_event(self.ev_run[b])
+        with torch.cuda.stream(self.s_out):
+            Yh.copy_(self.Y[b], non_blocking=True)
+            self.ev_out[b].record(self.s_out)
+        self.k += 1
+
+    def wait(self):
+        self.s_out.synchronize()
+
+
 class FGFRFTFunction(torch.autograd.Function):
     """Y = Q_L^{alpha} X with a hand-written backward (Props. 2-3).
 

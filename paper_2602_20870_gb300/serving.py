@@ -79,6 +79,13 @@ class _Batch:
     launched: float = 0.0
 
 
+def ncols(req) -> int:
+    """Signal columns of a request (1 for "assemble")."""
+    if req.kind == "assemble":
+        return 1
+    return req.cols if getattr(req, "cols", 0) else req.X.shape[0]
+
+
 def request_bytes(N: int, kind: str, cols: int) -> int:
     """Device bytes a request holds while in flight (inputs, outputs, scratch share)."""
     if kind == "assemble":
@@ -116,9 +123,8 @@ class Server:
         N = g.plan.N
         if req.L > g.plan.L_max:
             raise ValueError("L exceeds the graph's stored L_max")
-        cols = 1 if req.kind == "assemble" else req.X.shape[0]
         p = _Pending(req, Future(), self.now() if arrival is None else arrival,
-                     request_bytes(N, req.kind, cols))
+                     request_bytes(N, req.kind, ncols(req)))
         if p.nbytes > self.budget:
             p.fut.set_exception(MemoryError("request larger than the HBM budget"))
             return p.fut
@@ -169,8 +175,8 @@ class Server:
             if key not in groups:
                 inflight_per_graph[g] = inflight_per_graph.get(g, 0) + 1
             cur = groups.setdefault(key, [])
-            cols = sum(1 if q.req.kind == "assemble" else q.req.X.shape[0] for q in cur)
-            add = 1 if p.req.kind == "assemble" else p.req.X.shape[0]
+            cols = sum(ncols(q.req) for q in cur)
+            add = ncols(p.req)
             if cur and cols + add > self.max_cols:
                 continue
             cur.append(p)
@@ -209,7 +215,7 @@ class Server:
                     Y, D = plan.forward_dual(alphas, X, L, path=path, stream=stream)
                 off = 0
                 for it in items:
-                    c = it.req.X.shape[0]
+                    c = ncols(it.req)
                     per_item.append((Y[off:off + c], None if D is None else D[off:off + c]))
                     off += c
             ev = torch.cuda.Event()

@@ -224,18 +224,31 @@ def rgg_gft(n: int, seed: int, k: int = 12, sigma2: float = 0.01) -> np.ndarray:
 
 @dataclass
 class Request:
-    """One serving request: graph index, kind, orders, truncation order and signals."""
+    """One serving request: graph index, kind, orders, truncation order and signals.
+
+    ``X`` is (cols, N) complex128, or None for "assemble".  Requests made with
+    ``lazy=True`` draw their signals from (seed, rid) when ``X`` is first read."""
     rid: int
     arrival_s: float
     graph: int
     kind: str            # "apply" | "grad" | "assemble"
     alpha: np.ndarray    # one per signal column ("assemble": one order)
     L: int
-    X: np.ndarray | None  # (cols, N) complex128, None for "assemble"
+    _X: np.ndarray | None = None
+    cols: int = 0
+    N: int = 0
+    seed: int = 0
+
+    @property
+    def X(self):
+        if self._X is None and self.kind != "assemble" and self.cols:
+            rng = np.random.default_rng([self.seed, self.rid])
+            return complex_normal((self.cols, self.N), rng)
+        return self._X
 
 
 def serving_requests(sizes, count: int, rate_per_s: float, seed: int = 5,
-                     Ls=(16, 32, 64), max_cols: int = 64) -> list[Request]:
+                     Ls=(16, 32, 64), max_cols: int = 64, lazy: bool = False) -> list[Request]:
     """Poisson arrivals over resident graphs of the given sizes: graph uniform, alpha in
     [-2,2], L from ``Ls``, 1..max_cols N(0,1) signals, 60% apply / 30% grad / 10% assemble."""
     rng = np.random.default_rng(seed)
@@ -247,10 +260,10 @@ def serving_requests(sizes, count: int, rate_per_s: float, seed: int = 5,
         kind = "apply" if u < 0.6 else ("grad" if u < 0.9 else "assemble")
         L = int(rng.choice(Ls))
         if kind == "assemble":
-            out.append(Request(i, float(t[i]), g, kind, np.array([rng.uniform(-2, 2)]), L, None))
+            out.append(Request(i, float(t[i]), g, kind, np.array([rng.uniform(-2, 2)]), L))
             continue
         cols = int(rng.integers(1, max_cols + 1))
         a = np.full(cols, rng.uniform(-2.0, 2.0))
-        X = complex_normal((cols, sizes[g]), rng)
-        out.append(Request(i, float(t[i]), g, kind, a, L, X))
+        X = None if lazy else complex_normal((cols, sizes[g]), rng)
+        out.append(Request(i, float(t[i]), g, kind, a, L, X, cols, sizes[g], seed))
     return out
