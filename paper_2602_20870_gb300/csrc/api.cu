@@ -119,7 +119,9 @@ struct AssembleWork {
 AssembleWork carve_assemble(const fgfrft_plan_s* p, char* base, int64_t A, int L) {
   AssembleWork w;
   Carve c{base};
-  w.tensor = p->f16T != nullptr && A >= 2 && fg_tc_available();
+  // one order streams best through the c64 bulk-copy kernel; more orders (or no c64
+  // stack) use the tensor-core GEMM over the entry-major stack
+  w.tensor = p->f16T != nullptr && (A >= 2 || p->c64 == nullptr) && fg_tc_available();
   w.alpha_dev = c.take<double>((size_t)A);
   if (w.tensor) {
     w.coef = c.take<float2>((size_t)A * p->nblk);
@@ -165,8 +167,9 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
   }
   cudaError_t e = fg_coeffs(alpha_dev, (int)A, L, false, w.coef, nullptr, A, 1, s);
   if (e != cudaSuccess) return e;
-  if (A == 1 && Qs == nullptr)
-    return fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, w.coef, Qc, p->dstatus, s);
+  if (A == 1)  // one order: the bulk-copy streaming kernel, c64 or split output
+    return fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, w.coef, Qc, p->dstatus, s, Qs, p->N,
+                              p->Np, p->plane_elems);
   return fg_assemble_multi(p->c64, p->blk_elems, b0, nb, pb, p->N, (int)A, w.coef, Qc, Qs, p->Np, p->plane_elems,
                            p->dstatus, s);
 }

@@ -24,11 +24,16 @@ struct K1Smem {
   uint64_t full[K1_STAGES];
 };
 
+// SPLIT: Q is written as four fp16 planes (scaled by 2^FG_SPLIT_SHIFT, hi/lo) of N rows
+// with pitch Np instead of c64.
+template <bool SPLIT>
 __global__ void __launch_bounds__(K1_THREADS) assemble_single_kernel(const float2* __restrict__ stack,
                                                                      int64_t blk_elems, int b0, int nb_pow,
                                                                      int p_blk, int64_t NN,
                                                                      const float2* __restrict__ coef,
-                                                                     float2* __restrict__ Q, uint32_t* status) {
+                                                                     float2* __restrict__ Q, __half* __restrict__ Qs,
+                                                                     int64_t N, int64_t Np, int64_t plane_elems,
+                                                                     uint32_t* status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   K1Smem& sm = *reinterpret_cast<K1Smem*>(smem_raw);
   const int nblk = nb_pow + (p_blk >= 0 ? 1 : 0);
@@ -96,8 +101,28 @@ __global__ void __launch_bounds__(K1_THREADS) assemble_single_kernel(const float
 #pragma unroll
       for (int v = 0; v < K1_PER_THREAD / 2; ++v) {
         const int64_t e = e0 + 2 * (tid + (int64_t)v * K1_THREADS);
-        if (e < NN) Q[e] = acc[2 * v];
-        if (e + 1 < NN) Q[e + 1] = acc[2 * v + 1];
+        if (!SPLIT) {
+          if (e < NN) Q[e] = acc[2 * v];
+          if (e + 1 < NN) Q[e + 1] = acc[2 * v + 1];
+        } else {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int64_t g = e + u;
+            if (g < NN) {
+              const int64_t i = g / N, k = g - (g / N) * N;
+              const float sc = (float)(1 << FG_SPLIT_SHIFT);
+              const float re = acc[2 * v + u].x * sc, im = acc[2 * v + u].y * sc;
+              const __half2 hi = __floats2half2_rn(re, im);
+              const float2 hf = __half22float2(hi);
+              const __half2 lo = __floats2half2_rn(re - hf.x, im - hf.y);
+              __half* q = Qs + i * Np + k;
+              q[0] = __low2half(hi);
+              q[plane_elems] = __low2half(lo);
+              q[2 * plane_elems] = __high2half(hi);
+              q[3 * plane_elems] = __high2half(lo);
+            }
+          }
+        }
         acc[2 * v] = make_float2(0.f, 0.f);
         acc[2 * v + 1] = make_float2(0.f, 0.f);
       }
@@ -303,23 +328,24 @@ cudaError_t launch_multi(const float2* stack, int64_t blk_elems, int b0, int nb_
 }  // namespace
 
 cudaError_t fg_assemble_single(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk, int64_t NN,
-                               const float2* coef, float2* Q, uint32_t* status, cudaStream_t s) {
+                               const float2* coef, float2* Q, uint32_t* status, cudaStream_t s, __half* Qs,
+                               int64_t N, int64_t Np, int64_t plane_elems) {
   const int nblk = nb_pow + (p_blk >= 0 ? 1 : 0);
   if (nblk > K1_MAXBLK) return cudaErrorInvalidValue;
   const size_t smem = sizeof(K1Smem);
-  cudaError_t e =
-      cudaFuncSetAttribute(assemble_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = Qs ? assemble_single_kernel<true> : assemble_single_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assemble_single_kernel, K1_THREADS, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K1_THREADS, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int64_t ntiles = (NN + K1_CHUNK - 1) / K1_CHUNK;
   int64_t grid = (int64_t)num_sms() * per_sm;
   if (grid > ntiles) grid = ntiles;
   FgTimed timed(FGFRFT_KC_ASSEMBLE_SINGLE, s);
-  assemble_single_kernel<<<(unsigned)grid, K1_THREADS, smem, s>>>(stack, blk_elems, b0, nb_pow, p_blk, NN, coef, Q,
-                                                                   status);
+  kern<<<(unsigned)grid, K1_THREADS, smem, s>>>(stack, blk_elems, b0, nb_pow, p_blk, NN, coef, Q, Qs, N, Np,
+                                                plane_elems, status);
   fg_note_launch(FGFRFT_KC_ASSEMBLE_SINGLE);
   return cudaGetLastError();
 }

@@ -42,22 +42,28 @@ constexpr int TC_EPI_WARP0 = 2;
 constexpr int TC_BN_MAX = 128;
 
 // Column-tile width BN (complex columns per tile): 128, or 64 for few columns.
-template <int BN>
+// RB ("resident B"): every tile uses the same B columns (one column tile), so all k-chunks
+// of B are loaded once per CTA into shared memory and the ring stages carry A only.
+constexpr int TC_RB_MAXCH = 5;  // resident-B mode: at most 5 k-chunks (K <= 160)
+template <int BN, bool RB = false>
 struct TcCfg {
   static constexpr int PLANE_B = BN * TC_KC * 2;
-  static constexpr int STAGE_BYTES = 4 * TC_PLANE_A + 4 * PLANE_B;
-  static constexpr int STAGES = BN == 128 ? 3 : 4;
+  static constexpr int STAGE_BYTES = 4 * TC_PLANE_A + (RB ? 0 : 4 * PLANE_B);
+  static constexpr int STAGES = RB ? 4 : (BN == 128 ? 3 : 4);
+  static constexpr int RES_BYTES = RB ? TC_RB_MAXCH * 4 * PLANE_B : 1024;
   static constexpr int TMEM_COLS = 4 * BN;  // 2 buffers x [re BN | im BN]
   // kind::f16 instruction descriptor: D f32, A/B f16, both K-major, N = BN, M = 128.
   static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
   static constexpr uint32_t IDESC_NEG_A = IDESC | (1u << 13);
 };
 
-template <int BN>
+template <int BN, bool RB = false>
 struct __align__(1024) TcSmem {
-  uint8_t stage[TcCfg<BN>::STAGES][TcCfg<BN>::STAGE_BYTES];
-  uint64_t full[TcCfg<BN>::STAGES];
-  uint64_t empty[TcCfg<BN>::STAGES];
+  uint8_t stage[TcCfg<BN, RB>::STAGES][TcCfg<BN, RB>::STAGE_BYTES];
+  uint8_t bres[TcCfg<BN, RB>::RES_BYTES];  // resident B: [chunk][4 planes][BN rows x 64 B]
+  uint64_t full[TcCfg<BN, RB>::STAGES];
+  uint64_t empty[TcCfg<BN, RB>::STAGES];
+  uint64_t bfull;
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t drain;
@@ -153,10 +159,10 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, Smem& sm
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory"); }
 
-template <int BN>
+template <int BN, bool RB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
-  using Cfg = TcCfg<BN>;
+  using Cfg = TcCfg<BN, RB>;
   constexpr int TC_STAGES = Cfg::STAGES;
   constexpr int TC_BN = BN;
   constexpr int TC_PLANE_B = Cfg::PLANE_B;
@@ -165,8 +171,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr uint32_t kIdesc = Cfg::IDESC;
   constexpr uint32_t kIdescNegA = Cfg::IDESC_NEG_A;
   extern __shared__ uint8_t smem_raw[];
-  TcSmem<BN>& sm =
-      *reinterpret_cast<TcSmem<BN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TcSmem<BN, RB>& sm =
+      *reinterpret_cast<TcSmem<BN, RB>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
@@ -180,6 +186,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&sm.tempty[b], TC_EPI_WARPS);
     }
     mbar_init(&sm.drain, 1);
+    mbar_init(&sm.bfull, 1);
     sm.abort = 0;
     fence_barrier_init();
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
@@ -203,6 +210,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t issued[TC_STAGES] = {};
       bool ok = true;
       int4 next = blockIdx.x < p.ntiles ? p.tiles[blockIdx.x] : make_int4(0, 0, 0, 0);
+      bool b_issued = false;
+      if (RB && blockIdx.x < p.ntiles) {  // all k-chunks of B, once
+        mbar_arrive_expect_tx(&sm.bfull, (uint32_t)(p.kchunks * 4 * TC_PLANE_B));
+        for (int kc = 0; kc < p.kchunks; ++kc)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            tma_load_3d(sm.bres + (kc * 4 + q) * TC_PLANE_B, &tmB, kc * TC_KC, next.z, q, &sm.bfull);
+        b_issued = true;
+      }
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
         const int4 tile = next;
         if (t + (int)gridDim.x < p.ntiles) next = p.tiles[t + gridDim.x];  // prefetch
@@ -221,13 +237,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int k0 = kc * TC_KC;
 #pragma unroll
             for (int q = 0; q < 4; ++q) tma_load_3d(st + q * TC_PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
+            if (!RB) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              tma_load_3d(st + 4 * TC_PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
+              for (int q = 0; q < 4; ++q)
+                tma_load_3d(st + 4 * TC_PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
+            }
           }
         }
       }
       if (!ok) {  // wait (bounded) until every issued copy has landed
+        if (b_issued) {
+          const uint64_t t0 = global_timer_ns();
+          while (!mbar_try_wait(&sm.bfull, 0) && global_timer_ns() - t0 < FG_WAIT_LIMIT_NS) {
+          }
+        }
         for (int s = 0; s < TC_STAGES; ++s) {
           if (!issued[s]) continue;
           const uint32_t par = (issued[s] - 1) & 1;
@@ -242,6 +265,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       uint32_t kit = 0, bc = 0;
       bool ok = true;
+      if (RB && blockIdx.x < p.ntiles) ok = tc_wait(&sm.bfull, 0, sm, p.status);
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
         for (int b = 0; ok && b < p.nblk; ++b, ++bc) {
           const uint32_t buf = bc & 1, tph = (bc >> 1) & 1;
@@ -261,7 +285,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             fence_tc_after();
             const uint32_t sa = smem_u32(sm.stage[s]);
-            const uint32_t sb = sa + 4 * TC_PLANE_A;
+            const uint32_t sb = RB ? smem_u32(sm.bres + kc * 4 * TC_PLANE_B) : sa + 4 * TC_PLANE_A;
 #pragma unroll
             for (int kk = 0; kk < TC_KC / 16; ++kk) {
               const uint32_t off = kk * 32;  // 16 fp16 along k
@@ -473,23 +497,25 @@ int sm_count() {
   return n;
 }
 
-template <int BN>
+template <int BN, bool RB>
 cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, int ntiles, const TcParams& p, cudaStream_t s,
                       int kclass) {
-  const size_t smem = sizeof(TcSmem<BN>) + 1024;
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = sizeof(TcSmem<BN, RB>) + 1024;
+  cudaError_t e =
+      cudaFuncSetAttribute(tc_gemm_kernel<BN, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = std::min<int>(ntiles, sm_count());
   FgTimed timed(kclass, s);
-  tc_gemm_kernel<BN><<<grid, TC_THREADS, smem, s>>>(mA, mB, p);
+  tc_gemm_kernel<BN, RB><<<grid, TC_THREADS, smem, s>>>(mA, mB, p);
   fg_note_launch(kclass);
   return cudaGetLastError();
 }
 
 // bn: column-tile width (64 or 128); the B tensor map's box must have bn rows.
+// resident_b: every tile has the same columns (needs bn == 64 and kchunks <= TC_RB_MAXCH).
 cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vector<int4>& tiles, TcParams p,
                    void* scratch, size_t scratch_bytes, cudaStream_t s, int kclass = FGFRFT_KC_TC_GEMM,
-                   int bn = 128) {
+                   int bn = 128, bool resident_b = false) {
   if (tiles.empty()) return cudaSuccess;
   const size_t tbytes = tiles.size() * sizeof(int4);
   if (tbytes > scratch_bytes) return cudaErrorInvalidValue;
@@ -497,7 +523,12 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vect
   if (e != cudaSuccess) return e;
   p.tiles = (const int4*)scratch;
   p.ntiles = (int)tiles.size();
-  return bn == 64 ? launch_bn<64>(mA, mB, p.ntiles, p, s, kclass) : launch_bn<128>(mA, mB, p.ntiles, p, s, kclass);
+  if (resident_b) {
+    if (bn != 64 || p.kchunks > TC_RB_MAXCH) return cudaErrorInvalidValue;
+    return launch_bn<64, true>(mA, mB, p.ntiles, p, s, kclass);
+  }
+  return bn == 64 ? launch_bn<64, false>(mA, mB, p.ntiles, p, s, kclass)
+                  : launch_bn<128, false>(mA, mB, p.ntiles, p, s, kclass);
 }
 
 }  // namespace
@@ -612,7 +643,9 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   p.qplane = a.plane_elems;
   p.col_exp = a.col_exp;
   p.status = a.status;
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, bn);
+  // one column tile (A <= 64): the coefficient operand stays resident in shared memory
+  const bool rb = bn == 64 && p.kchunks <= TC_RB_MAXCH;
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, bn, rb);
 }
 
 size_t fg_tc_assemble_scratch_bytes(int64_t entries, int64_t A) {

@@ -178,8 +178,10 @@ cudaError_t fg_entry_major(const __half* f16, int nblk, int64_t N, int64_t Np, i
                            int64_t Kp, int64_t planeT, cudaStream_t s);
 
 // assemble.cu
+// Q (c64, [NN]) or, with Qs != NULL, split fp16 planes of N rows x Np (plane stride plane_elems).
 cudaError_t fg_assemble_single(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk,
-                               int64_t NN, const float2* coef, float2* Q, uint32_t* status, cudaStream_t s);
+                               int64_t NN, const float2* coef, float2* Q, uint32_t* status, cudaStream_t s,
+                               __half* Qs = nullptr, int64_t N = 0, int64_t Np = 0, int64_t plane_elems = 0);
 // Multi-order: Q_a = sum_b coef[b * A + a] * block_b for a < A; output c64 (Qc) or split fp16 (Qs).
 cudaError_t fg_assemble_multi(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk,
                               int64_t N, int A, const float2* coef, float2* Qc, __half* Qs, int64_t Np,

@@ -215,3 +215,17 @@ def test_integer_order_beyond_L_rejected_but_within_L_exact(FG, plans):
     Q = host(plan.assemble([3.0, -2.0], 16))
     assert rel(Q[0], O.integer_power(case.F, 3)) < TOL_FP32
     assert rel(Q[1], O.integer_power(case.F, -2)) < TOL_FP32
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=lambda c: c.name)
+def test_assembled_path_single_order(FG, plans, case):
+    """One order shared by every column: the assembled path assembles once (split output of
+    the streaming kernel) and runs the tensor-core GEMM."""
+    plan = plans[case.name]
+    rng = np.random.default_rng(17)
+    N = case.F.shape[0]
+    X = W.complex_normal((96, N), rng)
+    for a in (0.37, -1.4):
+        Y = host(plan.apply([a], dev(X), case.L_max, path="assembled"))
+        ref = O.apply_power(case.F, a, case.L_max, X.T, case.P).T
+        assert rel(Y, ref) < TOL_SPLIT
