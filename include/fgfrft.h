@@ -160,6 +160,12 @@ const void* fgfrft_plan_block(fgfrft_plan p, int storage, int l, int64_t* block_
  * FGFRFT_OK, or FGFRFT_ERR_TIMEOUT when a kernel's bounded wait ran out. */
 int fgfrft_plan_status(fgfrft_plan p, void* stream);
 
+/* 1 if F was real (all imaginary parts exactly 0) and no W was supplied: every stored
+ * block is then real and the tensor-core paths skip the imaginary planes (6 instead of
+ * 12 MMAs per k16 step; the skipped products are exact zeros).  0 otherwise;
+ * -FGFRFT_ERR_INVALID_ARG for a NULL plan. */
+int fgfrft_plan_real(fgfrft_plan p);
+
 /* Release the host record of a plan.  Frees nothing caller-owned. */
 int fgfrft_plan_destroy(fgfrft_plan p);
 

@@ -163,10 +163,15 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
     ta.scratch = w.scratch;
     ta.scratch_bytes = w.scratch_bytes;
     ta.status = p->dstatus;
+    ta.real_a = p->real;
+    ta.skip_im = p->real && p->r_neg1 == 0 && Qs != nullptr;
     return fg_tc_assemble(ta, s);
   }
   cudaError_t e = fg_coeffs(alpha_dev, (int)A, L, false, w.coef, nullptr, A, 1, s);
   if (e != cudaSuccess) return e;
+  if (A == 1 && p->real && p->f16)  // one order, real F: stream the two real split planes
+    return fg_assemble_single_real(p->f16, 4 * p->plane_elems, p->plane_elems, b0, nb, pb, p->N, p->Np, w.coef, Qc,
+                                   Qs, p->plane_elems, p->r_neg1 > 0, p->dstatus, s);
   if (A == 1)  // one order: the bulk-copy streaming kernel, c64 or split output
     return fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, w.coef, Qc, p->dstatus, s, Qs, p->N,
                               p->Np, p->plane_elems);
@@ -328,6 +333,10 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
       fg_ztrace_fro(N, Am, nullptr, red, s) || !readback())
     return fail(FGFRFT_ERR_CUDA);
   if (!(sqrt(h[1]) / sqrt((double)N) <= 1e-8)) return fail(FGFRFT_ERR_NOT_UNITARY);
+  // real F: every power and the projector are real (FP64 products of real matrices keep
+  // exact zero imaginary parts), so the tensor-core paths may skip the imaginary planes
+  if (fg_zimag_sq(N, (const double2*)F_dev, red, s) || !readback()) return fail(FGFRFT_ERR_CUDA);
+  p->real = (h[0] == 0.0) && (!W_dev);
 
   // (2) projector P onto the lambda = -1 eigenspace, into Cm
   int squarings = 0;
@@ -448,6 +457,11 @@ int fgfrft_plan_status(fgfrft_plan p, void* stream) {
   }
   if (w & FG_STATUS_WAIT_TIMEOUT) return FGFRFT_ERR_TIMEOUT;
   return FGFRFT_OK;
+}
+
+int fgfrft_plan_real(fgfrft_plan p) {
+  if (!p) return -FGFRFT_ERR_INVALID_ARG;
+  return p->real ? 1 : 0;
 }
 
 int fgfrft_plan_destroy(fgfrft_plan p) {
@@ -586,6 +600,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       ta.scratch = w.tc_scratch;
       ta.scratch_bytes = w.tc_scratch_bytes;
       ta.status = p->dstatus;
+      ta.real_a = p->real && p->r_neg1 == 0;  // Q = R + j sin(pi a) P is real when P = 0
       CK(fg_tc_grouped_apply(ta, s));
       return FGFRFT_OK;
     }
@@ -613,6 +628,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       ta.scratch = w.tc_scratch;
       ta.scratch_bytes = w.tc_scratch_bytes;
       ta.status = p->dstatus;
+      ta.real_a = p->real;
       CK(fg_tc_stacked_apply(ta, s));
       return FGFRFT_OK;
     }

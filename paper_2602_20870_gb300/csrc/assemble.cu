@@ -141,6 +141,144 @@ __global__ void __launch_bounds__(K1_THREADS) assemble_single_kernel(const float
 }
 
 // ---------------------------------------------------------------------------
+// K1 for real F: the stored blocks are real, so the assembly streams only their two real
+// split planes (fp16 hi/lo of 2^12 M, 4 bytes per entry instead of 8):
+//   Re Q = sum_l c_l M_l + cos(pi a) P,   Im Q = sin(pi a) P.
+// The planes are N rows of pitch Np; the kernel streams all N * Np slots of a plane and
+// skips the padding columns on output.
+// ---------------------------------------------------------------------------
+constexpr int KR_CHUNK = 4096;  // entries per tile: 2 planes x 8 KB per block
+constexpr int KR_STAGES = 6;
+constexpr int KR_EPT = KR_CHUNK / K1_THREADS;  // 16 entries per thread
+
+struct KRSmem {
+  uint4 ring[KR_STAGES][2][KR_CHUNK / 8];  // [stage][hi, lo][8 halves]
+  float2 coef[K1_MAXBLK];
+  uint64_t full[KR_STAGES];
+};
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(K1_THREADS) assemble_single_real_kernel(
+    const __half* __restrict__ planes, int64_t blk_stride, int64_t plane_elems, int b0, int nb_pow, int p_blk,
+    int64_t N, int64_t Np, const float2* __restrict__ coef, float2* __restrict__ Q, __half* __restrict__ Qs,
+    int64_t q_plane, int write_im, uint32_t* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  KRSmem& sm = *reinterpret_cast<KRSmem*>(smem_raw);
+  const int nblk = nb_pow + (p_blk >= 0 ? 1 : 0);
+  const int tid = threadIdx.x;
+  for (int b = tid; b < nblk; b += K1_THREADS) sm.coef[b] = coef[b];
+  if (tid == 0) {
+    for (int s = 0; s < KR_STAGES; ++s) mbar_init(&sm.full[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const int64_t total = N * Np;  // slots per plane (N rows of pitch Np)
+  const int64_t ntiles = (total + KR_CHUNK - 1) / KR_CHUNK;
+  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t items = my_tiles * nblk;
+  uint64_t policy = 0;
+  if (tid == 0) policy = policy_evict_first();
+  auto issue = [&](int64_t item) {
+    const int s = (int)(item % KR_STAGES);
+    const int64_t t = blockIdx.x + (item / nblk) * gridDim.x;
+    const int b = (int)(item % nblk);
+    const int blk = b < nb_pow ? b0 + b : p_blk;
+    const int64_t e0 = t * KR_CHUNK;
+    const int64_t cnt = (total - e0) < KR_CHUNK ? (total - e0) : KR_CHUNK;
+    // plane_elems is padded to 128 slots, so rounding the byte count up to 16 stays inside it
+    const uint32_t bytes = (uint32_t)(((cnt * 2) + 15) & ~int64_t(15));
+    mbar_arrive_expect_tx(&sm.full[s], 2 * bytes);
+    const __half* src = planes + (int64_t)blk * blk_stride + e0;
+    bulk_g2s_evict_first(&sm.ring[s][0][0], src, bytes, &sm.full[s], policy);
+    bulk_g2s_evict_first(&sm.ring[s][1][0], src + plane_elems, bytes, &sm.full[s], policy);
+  };
+  if (tid == 0) {
+    const int64_t pre = items < KR_STAGES ? items : KR_STAGES;
+    for (int64_t it = 0; it < pre; ++it) issue(it);
+  }
+  const float inv = 1.0f / (float)(1 << FG_SPLIT_SHIFT);
+  float acc[KR_EPT];
+  float accp[KR_EPT];  // the P block (real), kept apart for its complex coefficient
+#pragma unroll
+  for (int e = 0; e < KR_EPT; ++e) acc[e] = accp[e] = 0.f;
+  bool ok = true;
+  for (int64_t it = 0; it < items; ++it) {
+    const int s = (int)(it % KR_STAGES);
+    const uint32_t parity = (uint32_t)((it / KR_STAGES) & 1);
+    const int b = (int)(it % nblk);
+    if (ok) ok = mbar_wait(&sm.full[s], parity, status);
+    if (ok) {
+      const float c = b < nb_pow ? sm.coef[b].x * inv : 0.f;
+#pragma unroll
+      for (int v = 0; v < KR_EPT / 8; ++v) {
+        const uint4 hv = sm.ring[s][0][tid + v * K1_THREADS];
+        const uint4 lv = sm.ring[s][1][tid + v * K1_THREADS];
+        const __half2* h2 = reinterpret_cast<const __half2*>(&hv);
+        const __half2* l2 = reinterpret_cast<const __half2*>(&lv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 hf = __half22float2(h2[q]), lf = __half22float2(l2[q]);
+          const float x0 = hf.x + lf.x, x1 = hf.y + lf.y;
+          if (b < nb_pow) {
+            acc[8 * v + 2 * q] = fmaf(c, x0, acc[8 * v + 2 * q]);
+            acc[8 * v + 2 * q + 1] = fmaf(c, x1, acc[8 * v + 2 * q + 1]);
+          } else {
+            accp[8 * v + 2 * q] = x0 * inv;
+            accp[8 * v + 2 * q + 1] = x1 * inv;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && ok && it + KR_STAGES < items) issue(it + KR_STAGES);
+    if (b == nblk - 1) {
+      const int64_t t = blockIdx.x + (it / nblk) * gridDim.x;
+      const float2 cp = p_blk >= 0 ? sm.coef[nb_pow] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int v = 0; v < KR_EPT / 8; ++v) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e_loc = 8 * (tid + v * K1_THREADS) + u;  // slot within the tile
+          const int64_t slot = t * KR_CHUNK + e_loc;
+          const float re = acc[8 * v + u] + cp.x * accp[8 * v + u];
+          const float im = cp.y * accp[8 * v + u];
+          if (slot < total) {
+            const int64_t i = slot / Np, k = slot - (slot / Np) * Np;
+            if (k < N) {
+              if (!SPLIT) {
+                Q[i * N + k] = make_float2(re, im);
+              } else {
+                const float sc = (float)(1 << FG_SPLIT_SHIFT);
+                const __half2 hi = __floats2half2_rn(re * sc, im * sc);
+                const float2 hf = __half22float2(hi);
+                const __half2 lo = __floats2half2_rn(re * sc - hf.x, im * sc - hf.y);
+                __half* qq = Qs + slot;  // same pitch as the stored planes
+                qq[0] = __low2half(hi);
+                qq[q_plane] = __low2half(lo);
+                if (write_im) {
+                  qq[2 * q_plane] = __high2half(hi);
+                  qq[3 * q_plane] = __high2half(lo);
+                }
+              }
+            }
+          }
+          acc[8 * v + u] = 0.f;
+          accp[8 * v + u] = 0.f;
+        }
+      }
+    }
+  }
+  if (!ok && tid == 0) {
+    for (int s = 0; s < KR_STAGES; ++s) {
+      const uint64_t t0 = global_timer_ns();
+      while (!mbar_try_wait(&sm.full[s], 0) && !mbar_try_wait(&sm.full[s], 1)) {
+        if (global_timer_ns() - t0 > FG_WAIT_LIMIT_NS) break;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K2: up to 128 orders in one pass over the stack.  The orders form n_og groups of
 // 32; CTA c serves order group c mod n_og, and the n_og CTAs of a group walk the
 // same tile sequence at the same pace, so each stored tile is fetched from HBM once
@@ -366,4 +504,27 @@ cudaError_t fg_assemble_multi(const float2* stack, int64_t blk_elems, int b0, in
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t fg_assemble_single_real(const __half* planes, int64_t blk_stride, int64_t plane_elems, int b0,
+                                    int nb_pow, int p_blk, int64_t N, int64_t Np, const float2* coef, float2* Q,
+                                    __half* Qs, int64_t q_plane, bool write_im, uint32_t* status, cudaStream_t s) {
+  const int nblk = nb_pow + (p_blk >= 0 ? 1 : 0);
+  if (nblk > K1_MAXBLK) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(KRSmem);
+  auto kern = Qs ? assemble_single_real_kernel<true> : assemble_single_real_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K1_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t ntiles = (N * Np + KR_CHUNK - 1) / KR_CHUNK;
+  int64_t grid = (int64_t)num_sms() * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  FgTimed timed(FGFRFT_KC_ASSEMBLE_SINGLE, s);
+  kern<<<(unsigned)grid, K1_THREADS, smem, s>>>(planes, blk_stride, plane_elems, b0, nb_pow, p_blk, N, Np, coef, Q, Qs,
+                                                q_plane, write_im ? 1 : 0, status);
+  fg_note_launch(FGFRFT_KC_ASSEMBLE_SINGLE);
+  return cudaGetLastError();
 }

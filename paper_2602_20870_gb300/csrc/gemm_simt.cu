@@ -104,6 +104,81 @@ __global__ void __launch_bounds__(256) simt_stacked_kernel(SimtStackArgs a) {
   }
 }
 
+// Plain Y = A X (one block, no coefficients): 128 x 64 output tile, 8 x 4 complex per thread
+// (rows strided by 16 so that a warp's stores along i are contiguous), the next k-tile
+// prefetched into registers while the current one is multiplied from shared memory.
+constexpr int PBM = 128, PBN = 64, PBK = 16;
+
+__global__ void __launch_bounds__(256) cgemm_plain_kernel(SimtStackArgs a) {
+  __shared__ float2 As[PBK][PBM + 1];
+  __shared__ float2 Bs[PBK][PBN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * PBM, j0 = blockIdx.y * PBN;
+  const int N = a.N;
+  const float2* __restrict__ A = a.A;
+  float2 acc[8][4];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  float2 ra[8], rb[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int idx = tid + e * 256;
+      const int kk = idx & 15, rr = idx >> 4;
+      const int gi = i0 + rr, gk = k0 + kk;
+      ra[e] = (gi < N && gk < N) ? __ldg(A + (int64_t)gi * a.lda + gk) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = tid + e * 256;
+      const int kk = idx & 15, rr = idx >> 4;
+      const int gj = j0 + rr, gk = k0 + kk;
+      rb[e] = (gj < a.ncols && gk < N) ? __ldg(a.X + (int64_t)gj * N + gk) : make_float2(0.f, 0.f);
+    }
+  };
+  load(0);
+  for (int k0 = 0; k0 < N; k0 += PBK) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int idx = tid + e * 256;
+      As[idx & 15][idx >> 4] = ra[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = tid + e * 256;
+      Bs[idx & 15][idx >> 4] = rb[e];
+    }
+    __syncthreads();
+    if (k0 + PBK < N) load(k0 + PBK);
+#pragma unroll
+    for (int kk = 0; kk < PBK; ++kk) {
+      float2 av[8], bv[4];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) av[r] = As[kk][tx + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][ty + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cmac(acc[r][c], av[r], bv[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int gj = j0 + ty + 16 * c;
+    if (gj >= a.ncols) continue;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int gi = i0 + tx + 16 * r;
+      if (gi < N) a.Y[(int64_t)gj * N + gi] = acc[r][c];
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t fg_simt_stacked(const SimtStackArgs& a, cudaStream_t s) {
@@ -114,9 +189,11 @@ cudaError_t fg_simt_stacked(const SimtStackArgs& a, cudaStream_t s) {
   const bool dual = a.D != nullptr;
   FgTimed timed(FGFRFT_KC_SIMT_GEMM, s);
   fg_note_launch(FGFRFT_KC_SIMT_GEMM);
-  if (!scaled)
-    simt_stacked_kernel<false, false><<<grid, 256, 0, s>>>(a);
-  else if (!dual)
+  if (!scaled) {
+    dim3 pg((a.N + PBM - 1) / PBM, (a.ncols + PBN - 1) / PBN);
+    if (pg.y > 65535) return cudaErrorInvalidValue;
+    cgemm_plain_kernel<<<pg, 256, 0, s>>>(a);
+  } else if (!dual)
     simt_stacked_kernel<true, false><<<grid, 256, 0, s>>>(a);
   else
     simt_stacked_kernel<true, true><<<grid, 256, 0, s>>>(a);

@@ -45,11 +45,15 @@ constexpr int TC_BN_MAX = 128;
 // RB ("resident B"): every tile uses the same B columns (one column tile), so all k-chunks
 // of B are loaded once per CTA into shared memory and the ring stages carry A only.
 constexpr int TC_RB_MAXCH = 5;  // resident-B mode: at most 5 k-chunks (K <= 160)
-template <int BN, bool RB = false>
+// RA ("real A"): the A operand is real (its imaginary planes are zero), so only the two
+// real planes are loaded and each k16 step issues 6 MMAs (Ar*Xr, Ar*Xi) instead of 12.
+template <int BN, bool RB = false, bool RA = false>
 struct TcCfg {
   static constexpr int PLANE_B = BN * TC_KC * 2;
-  static constexpr int STAGE_BYTES = 4 * TC_PLANE_A + (RB ? 0 : 4 * PLANE_B);
-  static constexpr int STAGES = RB ? 4 : (BN == 128 ? 3 : 4);
+  static constexpr int A_PLANES = RA ? 2 : 4;
+  static constexpr int STAGE_BYTES = A_PLANES * TC_PLANE_A + (RB ? 0 : 4 * PLANE_B);
+  // as many stages as fit next to the resident operand (about 200 KB of shared memory)
+  static constexpr int STAGES = RB ? (RA ? 7 : 4) : (RA ? 4 : (BN == 128 ? 3 : 4));
   static constexpr int RES_BYTES = RB ? TC_RB_MAXCH * 4 * PLANE_B : 1024;
   static constexpr int TMEM_COLS = 4 * BN;  // 2 buffers x [re BN | im BN]
   // kind::f16 instruction descriptor: D f32, A/B f16, both K-major, N = BN, M = 128.
@@ -57,12 +61,12 @@ struct TcCfg {
   static constexpr uint32_t IDESC_NEG_A = IDESC | (1u << 13);
 };
 
-template <int BN, bool RB = false>
+template <int BN, bool RB = false, bool RA = false>
 struct __align__(1024) TcSmem {
-  uint8_t stage[TcCfg<BN, RB>::STAGES][TcCfg<BN, RB>::STAGE_BYTES];
-  uint8_t bres[TcCfg<BN, RB>::RES_BYTES];  // resident B: [chunk][4 planes][BN rows x 64 B]
-  uint64_t full[TcCfg<BN, RB>::STAGES];
-  uint64_t empty[TcCfg<BN, RB>::STAGES];
+  uint8_t stage[TcCfg<BN, RB, RA>::STAGES][TcCfg<BN, RB, RA>::STAGE_BYTES];
+  uint8_t bres[TcCfg<BN, RB, RA>::RES_BYTES];  // resident B: [chunk][4 planes][BN rows x 64 B]
+  uint64_t full[TcCfg<BN, RB, RA>::STAGES];
+  uint64_t empty[TcCfg<BN, RB, RA>::STAGES];
   uint64_t bfull;
   uint64_t tfull[2];
   uint64_t tempty[2];
@@ -84,6 +88,7 @@ struct TcParams {
   // value scaled by 2^FG_SPLIT_SHIFT and split into fp16 hi/lo
   __half* Qs;
   int64_t qN, qNp, qplane;
+  int skip_im;        // split output: the imaginary planes are zero and not written
   const float2* coef;
   const float2* coefd;
   int64_t ldcoef;
@@ -159,10 +164,11 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, Smem& sm
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory"); }
 
-template <int BN, bool RB>
+template <int BN, bool RB, bool RA>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
-  using Cfg = TcCfg<BN, RB>;
+  using Cfg = TcCfg<BN, RB, RA>;
+  constexpr int A_PLANES = Cfg::A_PLANES;
   constexpr int TC_STAGES = Cfg::STAGES;
   constexpr int TC_BN = BN;
   constexpr int TC_PLANE_B = Cfg::PLANE_B;
@@ -171,8 +177,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr uint32_t kIdesc = Cfg::IDESC;
   constexpr uint32_t kIdescNegA = Cfg::IDESC_NEG_A;
   extern __shared__ uint8_t smem_raw[];
-  TcSmem<BN, RB>& sm =
-      *reinterpret_cast<TcSmem<BN, RB>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TcSmem<BN, RB, RA>& sm =
+      *reinterpret_cast<TcSmem<BN, RB, RA>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
@@ -236,11 +242,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint8_t* st = sm.stage[s];
             const int k0 = kc * TC_KC;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tma_load_3d(st + q * TC_PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
+            for (int q = 0; q < A_PLANES; ++q)
+              tma_load_3d(st + q * TC_PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
             if (!RB) {
 #pragma unroll
               for (int q = 0; q < 4; ++q)
-                tma_load_3d(st + 4 * TC_PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
+                tma_load_3d(st + A_PLANES * TC_PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
             }
           }
         }
@@ -285,12 +292,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             fence_tc_after();
             const uint32_t sa = smem_u32(sm.stage[s]);
-            const uint32_t sb = RB ? smem_u32(sm.bres + kc * 4 * TC_PLANE_B) : sa + 4 * TC_PLANE_A;
+            const uint32_t sb = RB ? smem_u32(sm.bres + kc * 4 * TC_PLANE_B) : sa + A_PLANES * TC_PLANE_A;
 #pragma unroll
             for (int kk = 0; kk < TC_KC / 16; ++kk) {
               const uint32_t off = kk * 32;  // 16 fp16 along k
               const uint64_t arh = desc_sw64(sa + 0 * TC_PLANE_A + off), arl = desc_sw64(sa + 1 * TC_PLANE_A + off);
-              const uint64_t aih = desc_sw64(sa + 2 * TC_PLANE_A + off), ail = desc_sw64(sa + 3 * TC_PLANE_A + off);
               const uint64_t brh = desc_sw64(sb + 0 * TC_PLANE_B + off), brl = desc_sw64(sb + 1 * TC_PLANE_B + off);
               const uint64_t bih = desc_sw64(sb + 2 * TC_PLANE_B + off), bil = desc_sw64(sb + 3 * TC_PLANE_B + off);
               const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
@@ -298,16 +304,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               umma(d_re, arh, brh, kIdesc, acc);
               umma(d_re, arh, brl, kIdesc, 1);
               umma(d_re, arl, brh, kIdesc, 1);
-              umma(d_re, aih, bih, kIdescNegA, 1);
-              umma(d_re, aih, bil, kIdescNegA, 1);
-              umma(d_re, ail, bih, kIdescNegA, 1);
               // imaginary part: Ar*Xi + Ai*Xr
               umma(d_im, arh, bih, kIdesc, acc);
               umma(d_im, arh, bil, kIdesc, 1);
               umma(d_im, arl, bih, kIdesc, 1);
-              umma(d_im, aih, brh, kIdesc, 1);
-              umma(d_im, aih, brl, kIdesc, 1);
-              umma(d_im, ail, brh, kIdesc, 1);
+              if (!RA) {
+                const uint64_t aih = desc_sw64(sa + 2 * TC_PLANE_A + off), ail = desc_sw64(sa + 3 * TC_PLANE_A + off);
+                umma(d_re, aih, bih, kIdescNegA, 1);
+                umma(d_re, aih, bil, kIdescNegA, 1);
+                umma(d_re, ail, bih, kIdescNegA, 1);
+                umma(d_im, aih, brh, kIdesc, 1);
+                umma(d_im, aih, brl, kIdesc, 1);
+                umma(d_im, ail, brh, kIdesc, 1);
+              }
             }
             umma_commit(&sm.empty[s]);  // stage s is free once these MMAs complete
           }
@@ -393,8 +402,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const __half2 lo = __floats2half2_rn(re - hf.x, im - hf.y);
                 qp[0] = __low2half(hi);
                 qp[pl] = __low2half(lo);
-                qp[2 * pl] = __high2half(hi);
-                qp[3 * pl] = __high2half(lo);
+                if (!p.skip_im) {
+                  qp[2 * pl] = __high2half(hi);
+                  qp[3 * pl] = __high2half(lo);
+                }
               }
               qp += 4 * pl;
             }
@@ -497,16 +508,16 @@ int sm_count() {
   return n;
 }
 
-template <int BN, bool RB>
+template <int BN, bool RB, bool RA>
 cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, int ntiles, const TcParams& p, cudaStream_t s,
                       int kclass) {
-  const size_t smem = sizeof(TcSmem<BN, RB>) + 1024;
+  const size_t smem = sizeof(TcSmem<BN, RB, RA>) + 1024;
   cudaError_t e =
-      cudaFuncSetAttribute(tc_gemm_kernel<BN, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(tc_gemm_kernel<BN, RB, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = std::min<int>(ntiles, sm_count());
   FgTimed timed(kclass, s);
-  tc_gemm_kernel<BN, RB><<<grid, TC_THREADS, smem, s>>>(mA, mB, p);
+  tc_gemm_kernel<BN, RB, RA><<<grid, TC_THREADS, smem, s>>>(mA, mB, p);
   fg_note_launch(kclass);
   return cudaGetLastError();
 }
@@ -515,7 +526,7 @@ cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, int ntiles, 
 // resident_b: every tile has the same columns (needs bn == 64 and kchunks <= TC_RB_MAXCH).
 cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vector<int4>& tiles, TcParams p,
                    void* scratch, size_t scratch_bytes, cudaStream_t s, int kclass = FGFRFT_KC_TC_GEMM,
-                   int bn = 128, bool resident_b = false) {
+                   int bn = 128, bool resident_b = false, bool real_a = false) {
   if (tiles.empty()) return cudaSuccess;
   const size_t tbytes = tiles.size() * sizeof(int4);
   if (tbytes > scratch_bytes) return cudaErrorInvalidValue;
@@ -525,10 +536,14 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vect
   p.ntiles = (int)tiles.size();
   if (resident_b) {
     if (bn != 64 || p.kchunks > TC_RB_MAXCH) return cudaErrorInvalidValue;
-    return launch_bn<64, true>(mA, mB, p.ntiles, p, s, kclass);
+    return real_a ? launch_bn<64, true, true>(mA, mB, p.ntiles, p, s, kclass)
+                  : launch_bn<64, true, false>(mA, mB, p.ntiles, p, s, kclass);
   }
-  return bn == 64 ? launch_bn<64, false>(mA, mB, p.ntiles, p, s, kclass)
-                  : launch_bn<128, false>(mA, mB, p.ntiles, p, s, kclass);
+  if (bn == 64)
+    return real_a ? launch_bn<64, false, true>(mA, mB, p.ntiles, p, s, kclass)
+                  : launch_bn<64, false, false>(mA, mB, p.ntiles, p, s, kclass);
+  return real_a ? launch_bn<128, false, true>(mA, mB, p.ntiles, p, s, kclass)
+                : launch_bn<128, false, false>(mA, mB, p.ntiles, p, s, kclass);
 }
 
 }  // namespace
@@ -578,7 +593,7 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   p.Y = a.Y;
   p.col_exp = a.col_exp;
   p.status = a.status;
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s);
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, 128, false, a.real_a);
 }
 
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
@@ -610,7 +625,7 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   p.D = a.D;
   p.col_exp = a.col_exp;
   p.status = a.status;
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s);
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, 128, false, a.real_a);
 }
 
 cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
@@ -643,9 +658,10 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   p.qplane = a.plane_elems;
   p.col_exp = a.col_exp;
   p.status = a.status;
+  p.skip_im = a.skip_im ? 1 : 0;
   // one column tile (A <= 64): the coefficient operand stays resident in shared memory
   const bool rb = bn == 64 && p.kchunks <= TC_RB_MAXCH;
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, bn, rb);
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, bn, rb, a.real_a);
 }
 
 size_t fg_tc_assemble_scratch_bytes(int64_t entries, int64_t A) {

@@ -28,6 +28,7 @@ struct fgfrft_plan_s {
   int r_neg1;
   double proj_residual;
   int squarings;
+  bool real;           // F (hence every stored block) is real: tensor paths skip the imaginary planes
 };
 
 // Index of the stored block holding M_l (l in -L_max..L_max) and of P.
@@ -172,6 +173,7 @@ cudaError_t fg_zaxpby_identity(int64_t N, double2 a, const double2* X, double2 b
 cudaError_t fg_zherm_sym(int64_t N, double2* S, cudaStream_t s);  // S <- (S + S^H)/2
 cudaError_t fg_zmcweeny(int64_t N, const double2* P2, const double2* P3, double2* P, cudaStream_t s);
 cudaError_t fg_ztrace_fro(int64_t N, const double2* S, const double2* Sub, double* out, cudaStream_t s);
+cudaError_t fg_zimag_sq(int64_t N, const double2* F, double* out, cudaStream_t s);  // out[0] = sum Im(F)^2
 cudaError_t fg_store_block(int64_t N, const double2* M, bool conj_transpose, float2* c64, __half* f16,
                            int64_t Np, int64_t plane_elems, cudaStream_t s);
 cudaError_t fg_entry_major(const __half* f16, int nblk, int64_t N, int64_t Np, int64_t plane_elems, __half* T,
@@ -182,6 +184,12 @@ cudaError_t fg_entry_major(const __half* f16, int nblk, int64_t N, int64_t Np, i
 cudaError_t fg_assemble_single(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk,
                                int64_t NN, const float2* coef, float2* Q, uint32_t* status, cudaStream_t s,
                                __half* Qs = nullptr, int64_t N = 0, int64_t Np = 0, int64_t plane_elems = 0);
+// Real F: one order from the two real split planes of each stored block (blk_stride halves
+// between blocks, plane_elems between planes); output c64 Q [N*N] or split planes Qs with
+// the stored pitch (imaginary planes only when write_im).
+cudaError_t fg_assemble_single_real(const __half* planes, int64_t blk_stride, int64_t plane_elems, int b0,
+                                    int nb_pow, int p_blk, int64_t N, int64_t Np, const float2* coef, float2* Q,
+                                    __half* Qs, int64_t q_plane, bool write_im, uint32_t* status, cudaStream_t s);
 // Multi-order: Q_a = sum_b coef[b * A + a] * block_b for a < A; output c64 (Qc) or split fp16 (Qs).
 cudaError_t fg_assemble_multi(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk,
                               int64_t N, int A, const float2* coef, float2* Qc, __half* Qs, int64_t Np,

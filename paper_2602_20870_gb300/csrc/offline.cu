@@ -249,6 +249,21 @@ __global__ void __launch_bounds__(256) entry_major_kernel(const __half* __restri
   }
 }
 
+// out[0] = sum of Im(F_ik)^2 (one block, fixed order): zero iff F is real.
+__global__ void __launch_bounds__(1024) zimag_sq_kernel(int64_t total, const double2* __restrict__ F, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) acc += F[t].y * F[t].y;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    out[0] = s;
+  }
+}
+
 inline int grid_for(int64_t total) {
   int64_t g = (total + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
@@ -311,6 +326,12 @@ cudaError_t fg_entry_major(const __half* f16, int nblk, int64_t N, int64_t Np, i
   dim3 grid((unsigned)((N * N + 31) / 32), (unsigned)((Kp + 31) / 32), 4);
   if (grid.y > 65535) return cudaErrorInvalidValue;
   entry_major_kernel<<<grid, 256, 0, s>>>(f16, nblk, N, Np, plane_elems, T, Kp, planeT);
+  fg_note_launch(FGFRFT_KC_OFFLINE);
+  return cudaGetLastError();
+}
+
+cudaError_t fg_zimag_sq(int64_t N, const double2* F, double* out, cudaStream_t s) {
+  zimag_sq_kernel<<<1, 1024, 0, s>>>(N * N, F, out);
   fg_note_launch(FGFRFT_KC_OFFLINE);
   return cudaGetLastError();
 }

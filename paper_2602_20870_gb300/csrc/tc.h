@@ -26,6 +26,7 @@ struct TcGroupedArgs {
   void* scratch;
   size_t scratch_bytes;
   uint32_t* status;
+  bool real_a;             // every Q_g is real (imaginary planes zero): 6 MMAs per k16 step
 };
 cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s);
 
@@ -47,6 +48,7 @@ struct TcStackedArgs {
   void* scratch;
   size_t scratch_bytes;
   uint32_t* status;
+  bool real_a;             // every stored block is real (real F)
 };
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s);
 
@@ -68,6 +70,8 @@ struct TcAssembleArgs {
   void* scratch;
   size_t scratch_bytes;
   uint32_t* status;
+  bool real_a;                // the stored blocks are real (real F)
+  bool skip_im;               // split output whose imaginary part is zero (real F, no -1 eigenvalue)
 };
 cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s);
 size_t fg_tc_assemble_scratch_bytes(int64_t entries, int64_t A);

@@ -43,6 +43,7 @@ SIGNATURES = {
     "fgfrft_plan_block": (_vp, [_vp, _i32, _i32, ctypes.POINTER(_i64)]),
     "fgfrft_plan_status": (_i32, [_vp, _vp]),
     "fgfrft_plan_destroy": (_i32, [_vp]),
+    "fgfrft_plan_real": (_i32, [_vp]),
     "fgfrft_work_bytes": (_sz, [_vp, _i32, _vp, _i64, _i32, _i32]),
     "fgfrft_assemble": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _sz, _vp]),
     "fgfrft_apply": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp, _sz, _vp]),
@@ -175,6 +176,7 @@ class Plan:
         _check(lib.fgfrft_plan_info(h, ctypes.byref(n64), ctypes.byref(lm), ctypes.byref(st), ctypes.byref(rn),
                                     ctypes.byref(res), ctypes.byref(sq), ctypes.byref(pb)), "fgfrft_plan_info")
         self.r_neg1, self.proj_residual, self.squarings, self.plan_bytes = rn.value, res.value, sq.value, pb.value
+        self.real = lib.fgfrft_plan_real(h) == 1
         self._work = None
 
     # ---------------------------------------------------------------- helpers

@@ -66,6 +66,8 @@ def plans(FG):
 def test_precompute_projector_and_powers(FG, plans, case):
     plan = plans[case.name]
     assert plan.r_neg1 == case.sp.r_neg1
+    # real F (the Laplacian GFTs, the cyclic shift) takes the real-operator tensor paths
+    assert plan.real == bool(np.all(case.F.imag == 0))
     P = host(plan.block(case.L_max + 1))
     assert np.abs(P - case.P).max() < 2e-6
     M = O.powers(case.F, case.L_max, case.P)
