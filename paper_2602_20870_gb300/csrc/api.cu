@@ -124,7 +124,6 @@ AssembleWork carve_assemble(const fgfrft_plan_s* p, char* base, int64_t A, int L
   w.tensor = p->f16T != nullptr && (A >= 2 || p->c64 == nullptr) && fg_tc_available();
   w.alpha_dev = c.take<double>((size_t)A);
   if (w.tensor) {
-    w.coef = c.take<float2>((size_t)A * p->nblk);
     w.Cs = c.take<__half>((size_t)4 * A * p->Kp);
     w.col_exp = c.take<int>((size_t)A);
     w.scratch_bytes = fg_tc_assemble_scratch_bytes(p->N * p->N, A);
@@ -141,9 +140,7 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
                          float2* Qc, __half* Qs, cudaStream_t s) {
   const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
   if (w.tensor) {
-    cudaError_t e = cudaMemsetAsync(w.coef, 0, (size_t)A * p->nblk * sizeof(float2), s);
-    if (e != cudaSuccess) return e;
-    e = fg_coeffs_stored(alpha_dev, (int)A, L, p->L_max, false, w.coef, 1, p->nblk, s);
+    cudaError_t e = fg_coeff_planes(alpha_dev, A, L, p->L_max, p->Kp, w.Cs, w.col_exp, s);
     if (e != cudaSuccess) return e;
     TcAssembleArgs ta{};
     ta.entry_stack = p->f16T;
@@ -151,7 +148,6 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
     ta.K = p->nblk;
     ta.Kp = p->Kp;
     ta.planeT = p->planeT;
-    ta.coefT = w.coef;
     ta.A = A;
     ta.Cs = w.Cs;
     ta.col_exp = w.col_exp;
@@ -165,6 +161,7 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
     ta.status = p->dstatus;
     ta.real_a = p->real;
     ta.skip_im = p->real && p->r_neg1 == 0 && Qs != nullptr;
+    ta.re_only = p->real && p->r_neg1 == 0;  // real blocks, P = 0: every Q_a is real
     return fg_tc_assemble(ta, s);
   }
   cudaError_t e = fg_coeffs(alpha_dev, (int)A, L, false, w.coef, nullptr, A, 1, s);
@@ -189,7 +186,9 @@ struct ApplyWork {
   __half* Qs = nullptr;
   __half* Xs = nullptr;
   int* col_exp = nullptr;
+  int* bimag = nullptr;
   double* partials = nullptr;
+  int2* gtab = nullptr;
   void* tc_scratch = nullptr;
   size_t tc_scratch_bytes = 0;
   int64_t xs_rows = 0;
@@ -207,7 +206,8 @@ ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int 
     case FGFRFT_PATH_PLAIN:
       w.group_alpha_dev = c.take<double>((size_t)groups);
       w.coef = c.take<float2>((size_t)nb * groups);
-      w.Qc = c.take<float2>((size_t)p->N * p->N);
+      w.Qc = c.take<float2>((size_t)groups * p->N * p->N);
+      w.gtab = c.take<int2>((size_t)groups);
       break;
     case FGFRFT_PATH_STACKED_FP32:
       w.coef = c.take<float2>((size_t)nb * B);
@@ -221,6 +221,7 @@ ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int 
       w.xs_rows = fg_tc_signal_rows(B, groups);
       w.Xs = c.take<__half>((size_t)4 * w.xs_rows * p->Np);
       w.col_exp = c.take<int>((size_t)w.xs_rows);
+      w.bimag = c.take<int>(1);
       w.tc_scratch_bytes = fg_tc_scratch_bytes(p->N, B, groups, 1);
       w.tc_scratch = c.take<char>(w.tc_scratch_bytes);
       if (base) w.asm_work = carve_assemble(p, w.asm_base, groups, L);
@@ -232,6 +233,7 @@ ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int 
       w.xs_rows = fg_tc_signal_rows(B, 1);
       w.Xs = c.take<__half>((size_t)4 * w.xs_rows * p->Np);
       w.col_exp = c.take<int>((size_t)w.xs_rows);
+      w.bimag = c.take<int>(1);
       w.tc_scratch_bytes = fg_tc_scratch_bytes(p->N, B, 1, nb);
       w.tc_scratch = c.take<char>(w.tc_scratch_bytes);
       break;
@@ -504,7 +506,7 @@ int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, v
   cudaStream_t s = (cudaStream_t)stream;
   AssembleWork w = carve_assemble(p, (char*)work, A, L);
   if (!w.tensor && !p->c64) return FGFRFT_ERR_UNSUPPORTED;
-  CK(cudaMemcpyAsync(w.alpha_dev, a.data(), (size_t)A * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(fg_h2d(w.alpha_dev, a.data(), (size_t)A * sizeof(double), s));
   CK(run_assemble(p, w, w.alpha_dev, A, L, (float2*)Q_dev, nullptr, s));
   return FGFRFT_OK;
 }
@@ -521,34 +523,50 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
   float2* Y = (float2*)Y_dev;
   switch (path) {
     case FGFRFT_PATH_PLAIN: {
-      if (!p->c64) return FGFRFT_ERR_UNSUPPORTED;
+      if (!p->c64 && !(p->real && p->f16)) return FGFRFT_ERR_UNSUPPORTED;
+      if (groups > 65535) return FGFRFT_ERR_UNSUPPORTED;
       std::vector<double> ga((size_t)groups);
       for (int64_t g = 0; g < groups; ++g) ga[(size_t)g] = a[(size_t)runs[(size_t)g].first];
-      CK(cudaMemcpyAsync(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(fg_h2d(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), s));
       // coefficient vectors one per order, contiguous: [groups][2L+2]
       CK(fg_coeffs(w.group_alpha_dev, (int)groups, L, false, w.coef, nullptr, 1, nb + 1, s));
+      // per order: stream the stack once into Q_g (one single-order assembly launch each;
+      // real F streams the two real split planes), then all Q_g X_g on FP32 CUDA cores in
+      // one batched launch
+      std::vector<int2> gt((size_t)groups);
+      int maxc = 0;
       for (int64_t g = 0; g < groups; ++g) {
-        // per order: stream the stack once into Q (K1), then Q X on FP32 CUDA cores
-        CK(fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, w.coef + g * (nb + 1), w.Qc,
-                              p->dstatus, s));
-        SimtStackArgs sa{};
-        sa.A = w.Qc;
-        sa.blk_elems = 0;
-        sa.lda = n;
-        sa.b0 = 0;
-        sa.nb_pow = 1;
-        sa.p_blk = -1;
-        sa.N = n;
-        sa.ncols = (int)runs[(size_t)g].second;
-        sa.X = X + runs[(size_t)g].first * p->N;
-        sa.Y = Y + runs[(size_t)g].first * p->N;
-        CK(fg_simt_stacked(sa, s));
+        float2* Qg = w.Qc + g * p->N * p->N;
+        if (p->real && p->f16)
+          CK(fg_assemble_single_real(p->f16, 4 * p->plane_elems, p->plane_elems, b0, nb, pb, p->N, p->Np,
+                                     w.coef + g * (nb + 1), Qg, nullptr, 0, true, p->dstatus, s));
+        else
+          CK(fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, w.coef + g * (nb + 1), Qg,
+                                p->dstatus, s));
+        gt[(size_t)g] = make_int2((int)runs[(size_t)g].first, (int)runs[(size_t)g].second);
+        maxc = std::max(maxc, (int)runs[(size_t)g].second);
       }
+      CK(fg_h2d(w.gtab, gt.data(), gt.size() * sizeof(int2), s));
+      SimtStackArgs sa{};
+      sa.A = w.Qc;
+      sa.lda = n;
+      sa.b0 = 0;
+      sa.nb_pow = 1;
+      sa.p_blk = -1;
+      sa.N = n;
+      sa.ncols = (int)B;
+      sa.X = X;
+      sa.Y = Y;
+      sa.groups = w.gtab;
+      sa.group_stride = p->N * p->N;
+      sa.max_group_cols = maxc;
+      sa.ngroups = (int)groups;
+      CK(fg_simt_stacked(sa, s));
       return FGFRFT_OK;
     }
     case FGFRFT_PATH_STACKED_FP32: {
       if (!p->c64) return FGFRFT_ERR_UNSUPPORTED;
-      CK(cudaMemcpyAsync(w.alpha_dev, a.data(), (size_t)B * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(fg_h2d(w.alpha_dev, a.data(), (size_t)B * sizeof(double), s));
       CK(fg_coeffs(w.alpha_dev, (int)B, L, false, w.coef, D_dev ? w.coefd : nullptr, B, 1, s));
       SimtStackArgs sa{};
       sa.A = p->c64;
@@ -581,7 +599,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
         gstart[(size_t)g] = runs[(size_t)g].first;
         gcount[(size_t)g] = runs[(size_t)g].second;
       }
-      CK(cudaMemcpyAsync(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(fg_h2d(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), s));
       CK(run_assemble(p, w.asm_work, w.group_alpha_dev, groups, L, nullptr, w.Qs, s));
       TcGroupedArgs ta{};
       ta.N = p->N;
@@ -601,12 +619,13 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       ta.scratch_bytes = w.tc_scratch_bytes;
       ta.status = p->dstatus;
       ta.real_a = p->real && p->r_neg1 == 0;  // Q = R + j sin(pi a) P is real when P = 0
+      ta.bimag = w.bimag;
       CK(fg_tc_grouped_apply(ta, s));
       return FGFRFT_OK;
     }
     case FGFRFT_PATH_STACKED: {
       if (!p->f16 || !fg_tc_available()) return FGFRFT_ERR_UNSUPPORTED;
-      CK(cudaMemcpyAsync(w.alpha_dev, a.data(), (size_t)B * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(fg_h2d(w.alpha_dev, a.data(), (size_t)B * sizeof(double), s));
       CK(fg_coeffs(w.alpha_dev, (int)B, L, false, w.coef, D_dev ? w.coefd : nullptr, B, 1, s));
       TcStackedArgs ta{};
       ta.N = p->N;
@@ -629,6 +648,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       ta.scratch_bytes = w.tc_scratch_bytes;
       ta.status = p->dstatus;
       ta.real_a = p->real;
+      ta.bimag = w.bimag;
       CK(fg_tc_stacked_apply(ta, s));
       return FGFRFT_OK;
     }

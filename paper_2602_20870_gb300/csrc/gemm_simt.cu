@@ -117,6 +117,14 @@ __global__ void __launch_bounds__(256) cgemm_plain_kernel(SimtStackArgs a) {
   const int i0 = blockIdx.x * PBM, j0 = blockIdx.y * PBN;
   const int N = a.N;
   const float2* __restrict__ A = a.A;
+  if (a.groups) {  // batched over column groups: this CTA's group
+    const int2 gr = a.groups[blockIdx.z];
+    if (j0 >= gr.y) return;
+    A += (int64_t)blockIdx.z * a.group_stride;
+    a.X += (int64_t)gr.x * N;
+    a.Y += (int64_t)gr.x * N;
+    a.ncols = gr.y;
+  }
   float2 acc[8][4];
 #pragma unroll
   for (int r = 0; r < 8; ++r)
@@ -190,8 +198,9 @@ cudaError_t fg_simt_stacked(const SimtStackArgs& a, cudaStream_t s) {
   FgTimed timed(FGFRFT_KC_SIMT_GEMM, s);
   fg_note_launch(FGFRFT_KC_SIMT_GEMM);
   if (!scaled) {
-    dim3 pg((a.N + PBM - 1) / PBM, (a.ncols + PBN - 1) / PBN);
-    if (pg.y > 65535) return cudaErrorInvalidValue;
+    const int cols = a.groups ? a.max_group_cols : a.ncols;
+    dim3 pg((a.N + PBM - 1) / PBM, (cols + PBN - 1) / PBN, a.groups ? a.ngroups : 1);
+    if (pg.y > 65535 || pg.z > 65535) return cudaErrorInvalidValue;
     cgemm_plain_kernel<<<pg, 256, 0, s>>>(a);
   } else if (!dual)
     simt_stacked_kernel<true, false><<<grid, 256, 0, s>>>(a);

@@ -51,34 +51,36 @@ template <int BN, bool RB = false, bool RA = false>
 struct TcCfg {
   static constexpr int PLANE_B = BN * TC_KC * 2;
   static constexpr int A_PLANES = RA ? 2 : 4;
-  static constexpr int STAGE_BYTES = A_PLANES * TC_PLANE_A + (RB ? 0 : 4 * PLANE_B);
-  // as many stages as fit next to the resident operand (about 200 KB of shared memory)
-  static constexpr int STAGES = RB ? (RA ? 7 : 4) : (RA ? 4 : (BN == 128 ? 3 : 4));
-  static constexpr int RES_BYTES = RB ? TC_RB_MAXCH * 4 * PLANE_B : 1024;
   static constexpr int TMEM_COLS = 4 * BN;  // 2 buffers x [re BN | im BN]
   // kind::f16 instruction descriptor: D f32, A/B f16, both K-major, N = BN, M = 128.
   static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
   static constexpr uint32_t IDESC_NEG_A = IDESC | (1u << 13);
 };
 
-template <int BN, bool RB = false, bool RA = false>
-struct __align__(1024) TcSmem {
-  uint8_t stage[TcCfg<BN, RB, RA>::STAGES][TcCfg<BN, RB, RA>::STAGE_BYTES];
-  uint8_t bres[TcCfg<BN, RB, RA>::RES_BYTES];  // resident B: [chunk][4 planes][BN rows x 64 B]
-  uint64_t full[TcCfg<BN, RB, RA>::STAGES];
-  uint64_t empty[TcCfg<BN, RB, RA>::STAGES];
+// Shared memory: this control block, then the resident B operand (RB: k-chunks x 4 planes),
+// then as many ring stages as fit in the rest (at most TC_MAXST).  A stage holds the A
+// planes and the B planes the launch needs (2 for a real B, else 4), so a launch with a
+// real operand gets a deeper ring from the same shared memory.
+constexpr int TC_MAXST = 16;
+struct __align__(1024) TcCtl {
+  uint64_t full[TC_MAXST];
+  uint64_t empty[TC_MAXST];
   uint64_t bfull;
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t drain;
   uint32_t tmem_base;
   volatile int abort;
-  float scale[BN];
+  float scale[TC_BN_MAX];
 };
+// the smallest ring the kernel runs with
+constexpr int TC_MIN_STAGES = 2;
 
 struct TcParams {
-  const int4* tiles;  // {row tile, A plane base (grouped), first column, end column}
+  const int4* tiles;  // {row tile, A plane base (grouped), first column, end column}; NULL: tile t
+                      // is row tile t of the single column tile [0, arith_cols)
   int ntiles;
+  int arith_cols;
   int nblk;           // blocks per tile
   int grouped;        // 1: A plane base from the tile, one block; 0: stacked blocks
   int b0, nb_pow, p_blk;
@@ -89,6 +91,9 @@ struct TcParams {
   __half* Qs;
   int64_t qN, qNp, qplane;
   int skip_im;        // split output: the imaginary planes are zero and not written
+  int re_only;        // real A and a real product: only the real accumulator is formed
+  int smem_bytes;     // dynamic shared memory usable from the 1024-aligned base
+  const int* bimag;   // NULL, or a device word that is 0 when every B column is real
   const float2* coef;
   const float2* coefd;
   int64_t ldcoef;
@@ -162,6 +167,10 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, Smem& sm
   }
 }
 
+__device__ __forceinline__ int4 tile_of(const TcParams& p, int t) {
+  return p.tiles ? p.tiles[t] : make_int4(t, 0, 0, p.arith_cols);
+}
+
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory"); }
 
 template <int BN, bool RB, bool RA>
@@ -169,21 +178,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
   using Cfg = TcCfg<BN, RB, RA>;
   constexpr int A_PLANES = Cfg::A_PLANES;
-  constexpr int TC_STAGES = Cfg::STAGES;
   constexpr int TC_BN = BN;
   constexpr int TC_PLANE_B = Cfg::PLANE_B;
-  constexpr int TC_STAGE_BYTES = Cfg::STAGE_BYTES;
   constexpr int TC_TMEM_COLS = Cfg::TMEM_COLS;
   constexpr uint32_t kIdesc = Cfg::IDESC;
   constexpr uint32_t kIdescNegA = Cfg::IDESC_NEG_A;
   extern __shared__ uint8_t smem_raw[];
-  TcSmem<BN, RB, RA>& sm =
-      *reinterpret_cast<TcSmem<BN, RB, RA>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* const sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TcCtl& sm = *reinterpret_cast<TcCtl*>(sbase);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // A real B (no column with an imaginary part) needs only its two real planes; with a
+  // real A the product is then real and only the real accumulator is formed.  The skipped
+  // products are exact zeros, so the results do not change.
+  const bool breal = p.bimag != nullptr && *p.bimag == 0;
+  const bool re_only = RA && (p.re_only || breal);
+  const int nbp = (re_only || breal) ? 2 : 4;  // B planes loaded
+  uint8_t* const bres = sbase + sizeof(TcCtl);  // resident B: [chunk][4 planes][BN rows x 64 B]
+  const int res_bytes = RB ? p.kchunks * 4 * TC_PLANE_B : 0;
+  uint8_t* const stages = bres + res_bytes;
+  const int stage_bytes = A_PLANES * TC_PLANE_A + (RB ? 0 : nbp * TC_PLANE_B);
+  const int nst = min(TC_MAXST, (p.smem_bytes - (int)sizeof(TcCtl) - res_bytes) / stage_bytes);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], 1);
     }
@@ -213,40 +231,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       uint32_t kit = 0;
-      uint32_t issued[TC_STAGES] = {};
+      uint32_t issued[TC_MAXST] = {};
       bool ok = true;
-      int4 next = blockIdx.x < p.ntiles ? p.tiles[blockIdx.x] : make_int4(0, 0, 0, 0);
+      int4 next = blockIdx.x < p.ntiles ? tile_of(p, blockIdx.x) : make_int4(0, 0, 0, 0);
       bool b_issued = false;
       if (RB && blockIdx.x < p.ntiles) {  // all k-chunks of B, once
-        mbar_arrive_expect_tx(&sm.bfull, (uint32_t)(p.kchunks * 4 * TC_PLANE_B));
+        mbar_arrive_expect_tx(&sm.bfull, (uint32_t)(p.kchunks * nbp * TC_PLANE_B));
         for (int kc = 0; kc < p.kchunks; ++kc)
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            tma_load_3d(sm.bres + (kc * 4 + q) * TC_PLANE_B, &tmB, kc * TC_KC, next.z, q, &sm.bfull);
+          for (int q = 0; q < nbp; ++q)
+            tma_load_3d(bres + (kc * 4 + q) * TC_PLANE_B, &tmB, kc * TC_KC, next.z, q, &sm.bfull);
         b_issued = true;
       }
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
         const int4 tile = next;
-        if (t + (int)gridDim.x < p.ntiles) next = p.tiles[t + gridDim.x];  // prefetch
+        if (t + (int)gridDim.x < p.ntiles) next = tile_of(p, t + gridDim.x);  // prefetch
         for (int b = 0; ok && b < p.nblk; ++b) {
           const int zA = p.grouped ? tile.y : 4 * (b < p.nb_pow ? p.b0 + b : p.p_blk);
           for (int kc = 0; kc < p.kchunks; ++kc, ++kit) {
-            const int s = (int)(kit % TC_STAGES);
-            const uint32_t ph = (kit / TC_STAGES) & 1;
+            const int s = (int)(kit % nst);
+            const uint32_t ph = (kit / nst) & 1;
             if (!tc_wait(&sm.empty[s], ph ^ 1, sm, p.status)) {
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(&sm.full[s], TC_STAGE_BYTES);
+            mbar_arrive_expect_tx(&sm.full[s], (uint32_t)stage_bytes);
             issued[s]++;
-            uint8_t* st = sm.stage[s];
+            uint8_t* st = stages + s * stage_bytes;
             const int k0 = kc * TC_KC;
 #pragma unroll
             for (int q = 0; q < A_PLANES; ++q)
               tma_load_3d(st + q * TC_PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
             if (!RB) {
-#pragma unroll
-              for (int q = 0; q < 4; ++q)
+              for (int q = 0; q < nbp; ++q)
                 tma_load_3d(st + A_PLANES * TC_PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
             }
           }
@@ -258,7 +274,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           while (!mbar_try_wait(&sm.bfull, 0) && global_timer_ns() - t0 < FG_WAIT_LIMIT_NS) {
           }
         }
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < nst; ++s) {
           if (!issued[s]) continue;
           const uint32_t par = (issued[s] - 1) & 1;
           const uint64_t t0 = global_timer_ns();
@@ -284,15 +300,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t d_re = tmem + buf * (2 * TC_BN);
           const uint32_t d_im = d_re + TC_BN;
           for (int kc = 0; kc < p.kchunks; ++kc, ++kit) {
-            const int s = (int)(kit % TC_STAGES);
-            const uint32_t ph = (kit / TC_STAGES) & 1;
+            const int s = (int)(kit % nst);
+            const uint32_t ph = (kit / nst) & 1;
             if (!tc_wait(&sm.full[s], ph, sm, p.status)) {
               ok = false;
               break;
             }
             fence_tc_after();
-            const uint32_t sa = smem_u32(sm.stage[s]);
-            const uint32_t sb = RB ? smem_u32(sm.bres + kc * 4 * TC_PLANE_B) : sa + A_PLANES * TC_PLANE_A;
+            const uint32_t sa = smem_u32(stages + s * stage_bytes);
+            const uint32_t sb = RB ? smem_u32(bres + kc * 4 * TC_PLANE_B) : sa + A_PLANES * TC_PLANE_A;
 #pragma unroll
             for (int kk = 0; kk < TC_KC / 16; ++kk) {
               const uint32_t off = kk * 32;  // 16 fp16 along k
@@ -304,6 +320,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               umma(d_re, arh, brh, kIdesc, acc);
               umma(d_re, arh, brl, kIdesc, 1);
               umma(d_re, arl, brh, kIdesc, 1);
+              if (re_only) continue;  // real product: no imaginary accumulator
+              if (breal) {            // complex A, real X: Im = Ai*Xr only
+                if (!RA) {
+                  const uint64_t aih = desc_sw64(sa + 2 * TC_PLANE_A + off), ail = desc_sw64(sa + 3 * TC_PLANE_A + off);
+                  umma(d_im, aih, brh, kIdesc, acc);
+                  umma(d_im, aih, brl, kIdesc, 1);
+                  umma(d_im, ail, brh, kIdesc, 1);
+                }
+                continue;
+              }
               // imaginary part: Ar*Xi + Ai*Xr
               umma(d_im, arh, bih, kIdesc, acc);
               umma(d_im, arh, bil, kIdesc, 1);
@@ -349,13 +375,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int e = j < tl.w ? p.col_exp[j] : 0;
       return ldexpf(1.0f, split_out ? -e : -(FG_SPLIT_SHIFT + e));
     };
-    int4 next = blockIdx.x < p.ntiles ? p.tiles[blockIdx.x] : make_int4(0, 0, 0, 0);
+    int4 next = blockIdx.x < p.ntiles ? tile_of(p, blockIdx.x) : make_int4(0, 0, 0, 0);
     float next_scale = blockIdx.x < p.ntiles ? col_scale(next) : 0.f;
     for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
       const int4 tile = next;
       const float my_scale = next_scale;
       if (t + (int)gridDim.x < p.ntiles) {
-        next = p.tiles[t + gridDim.x];
+        next = tile_of(p, t + gridDim.x);
         next_scale = col_scale(next);
       }
       epi_bar();
@@ -384,7 +410,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           uint32_t vr[32], vi[32];
           __syncwarp();  // tcgen05.ld is warp-collective: the whole warp converged
           tmem_ld32(base + cc * 32, vr);
-          tmem_ld32(base + TC_BN + cc * 32, vi);
+          if (re_only) {  // the imaginary accumulator was not formed: the product is real
+#pragma unroll
+            for (int c = 0; c < 32; ++c) vi[c] = 0u;
+          } else {
+            tmem_ld32(base + TC_BN + cc * 32, vi);
+          }
           tmem_wait_ld();
           if (!row_ok) {
             // rows past the end: nothing to store
@@ -497,6 +528,17 @@ bool make_map(CUtensorMap* m, const void* base, int64_t N, int64_t rows, int64_t
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+int smem_optin() {
+  static int n = 0;
+  if (!n) {
+    int d = 0, v = 0;
+    cudaGetDevice(&d);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
+    n = v > 0 ? v : 48 * 1024;
+  }
+  return n;
+}
+
 int sm_count() {
   static int n = 0;
   if (!n) {
@@ -511,13 +553,20 @@ int sm_count() {
 template <int BN, bool RB, bool RA>
 cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, int ntiles, const TcParams& p, cudaStream_t s,
                       int kclass) {
-  const size_t smem = sizeof(TcSmem<BN, RB, RA>) + 1024;
+  // all the shared memory a CTA may have (one CTA per SM); the kernel sizes its ring to it
+  const int smem = smem_optin();
+  using Cfg = TcCfg<BN, RB, RA>;
+  const int res_bytes = RB ? p.kchunks * 4 * Cfg::PLANE_B : 0;
+  const int worst_stage = Cfg::A_PLANES * TC_PLANE_A + (RB ? 0 : 4 * Cfg::PLANE_B);
+  TcParams q = p;
+  q.smem_bytes = smem - 1024;  // the kernel aligns its base up to 1024 bytes
+  if (q.smem_bytes - (int)sizeof(TcCtl) - res_bytes < TC_MIN_STAGES * worst_stage) return cudaErrorInvalidValue;
   cudaError_t e =
-      cudaFuncSetAttribute(tc_gemm_kernel<BN, RB, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(tc_gemm_kernel<BN, RB, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int grid = std::min<int>(ntiles, sm_count());
   FgTimed timed(kclass, s);
-  tc_gemm_kernel<BN, RB, RA><<<grid, TC_THREADS, smem, s>>>(mA, mB, p);
+  tc_gemm_kernel<BN, RB, RA><<<grid, TC_THREADS, smem, s>>>(mA, mB, q);
   fg_note_launch(kclass);
   return cudaGetLastError();
 }
@@ -527,13 +576,17 @@ cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, int ntiles, 
 cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vector<int4>& tiles, TcParams p,
                    void* scratch, size_t scratch_bytes, cudaStream_t s, int kclass = FGFRFT_KC_TC_GEMM,
                    int bn = 128, bool resident_b = false, bool real_a = false) {
-  if (tiles.empty()) return cudaSuccess;
-  const size_t tbytes = tiles.size() * sizeof(int4);
-  if (tbytes > scratch_bytes) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemcpyAsync(scratch, tiles.data(), tbytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
-  p.tiles = (const int4*)scratch;
-  p.ntiles = (int)tiles.size();
+  if (tiles.empty()) {
+    if (p.ntiles <= 0 || p.arith_cols <= 0) return cudaSuccess;  // arithmetic tiles (no table)
+    p.tiles = nullptr;
+  } else {
+    const size_t tbytes = tiles.size() * sizeof(int4);
+    if (tbytes > scratch_bytes) return cudaErrorInvalidValue;
+    cudaError_t e = fg_h2d(scratch, tiles.data(), tbytes, s);
+    if (e != cudaSuccess) return e;
+    p.tiles = (const int4*)scratch;
+    p.ntiles = (int)tiles.size();
+  }
   if (resident_b) {
     if (bn != 64 || p.kchunks > TC_RB_MAXCH) return cudaErrorInvalidValue;
     return real_a ? launch_bn<64, true, true>(mA, mB, p.ntiles, p, s, kclass)
@@ -571,7 +624,7 @@ size_t fg_tc_scratch_bytes(int64_t N, int64_t B, int64_t groups, int) {
 
 cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   if (a.N > (1 << 24) || a.B > (1 << 30)) return cudaErrorInvalidValue;
-  cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s);
+  cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s, a.bimag);
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
   if (!make_map(&mA, a.Qs, a.N, a.N, a.Np, 4 * a.groups, a.plane_elems, TC_BM) ||
@@ -593,12 +646,13 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   p.Y = a.Y;
   p.col_exp = a.col_exp;
   p.status = a.status;
+  p.bimag = a.bimag;
   return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, 128, false, a.real_a);
 }
 
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   if (a.N > (1 << 24) || a.B > (1 << 30)) return cudaErrorInvalidValue;
-  cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s);
+  cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s, a.bimag);
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
   const int64_t nplanes = 4 * (int64_t)(std::max(a.b0 + a.nb_pow, a.p_blk + 1));
@@ -625,6 +679,7 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   p.D = a.D;
   p.col_exp = a.col_exp;
   p.status = a.status;
+  p.bimag = a.bimag;
   return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, 128, false, a.real_a);
 }
 
@@ -633,8 +688,6 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   // entry-major split stack (K = all stored blocks), columns = the orders, whose
   // "signals" are their coefficient vectors over the stored blocks.
   if (a.entries > ((int64_t)1 << 37) || a.A > (1 << 20)) return cudaErrorInvalidValue;
-  cudaError_t e = fg_split_signals(a.coefT, a.A, a.K, a.Kp, a.A, a.Cs, a.col_exp, s);
-  if (e != cudaSuccess) return e;
   const int bn = a.A <= 64 ? 64 : 128;
   CUtensorMap mA, mB;
   if (!make_map(&mA, a.entry_stack, a.K, a.entries, a.Kp, 4, a.planeT, TC_BM) ||
@@ -643,10 +696,15 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   std::vector<int4> tiles;
   const int64_t row_tiles = (a.entries + TC_BM - 1) / TC_BM;
   if (row_tiles > INT32_MAX) return cudaErrorInvalidValue;
-  for (int64_t c = 0; c < a.A; c += bn)
-    for (int64_t rt = 0; rt < row_tiles; ++rt)
-      tiles.push_back(make_int4((int)rt, 0, (int)c, (int)std::min<int64_t>(c + bn, a.A)));
   TcParams p{};
+  if (a.A <= bn) {  // one column tile: tile t is row tile t, no table
+    p.ntiles = (int)row_tiles;
+    p.arith_cols = (int)a.A;
+  } else {
+    for (int64_t c = 0; c < a.A; c += bn)
+      for (int64_t rt = 0; rt < row_tiles; ++rt)
+        tiles.push_back(make_int4((int)rt, 0, (int)c, (int)std::min<int64_t>(c + bn, a.A)));
+  }
   p.nblk = 1;
   p.grouped = 1;
   p.rows = a.entries;
@@ -659,6 +717,7 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   p.col_exp = a.col_exp;
   p.status = a.status;
   p.skip_im = a.skip_im ? 1 : 0;
+  p.re_only = a.re_only && a.real_a ? 1 : 0;
   // one column tile (A <= 64): the coefficient operand stays resident in shared memory
   const bool rb = bn == 64 && p.kchunks <= TC_RB_MAXCH;
   return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, bn, rb, a.real_a);

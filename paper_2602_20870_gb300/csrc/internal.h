@@ -150,6 +150,10 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
 // instrumentation (timing.cu): per-class launch counters and optional event timing
 // ---------------------------------------------------------------------------
 void fg_note_launch(int cls, int n = 1);
+
+// Host-to-device copy of a small per-call table, staged through pinned memory so that the
+// call stays asynchronous (the source may be reused as soon as this returns).
+cudaError_t fg_h2d(void* dst, const void* src, size_t bytes, cudaStream_t s);
 struct FgTimed {  // records a CUDA event pair around its scope when timing is enabled
   FgTimed(int cls, cudaStream_t s);
   ~FgTimed();
@@ -209,6 +213,12 @@ struct SimtStackArgs {
   const float2* coef;    // [nblk][ldcoef] or NULL (unscaled single block)
   const float2* coefd;   // [nblk][ldcoef] for D
   int ldcoef;
+  // plain batched mode (coef == NULL): group g = blockIdx.z multiplies A + g * group_stride by
+  // columns groups[g].x .. groups[g].x + groups[g].y - 1 (device table); NULL = one group
+  const int2* groups;
+  int64_t group_stride;
+  int max_group_cols;
+  int ngroups;
 };
 cudaError_t fg_simt_stacked(const SimtStackArgs& a, cudaStream_t s);
 
@@ -216,12 +226,16 @@ cudaError_t fg_simt_stacked(const SimtStackArgs& a, cudaStream_t s);
 // coefficient (b, j) at b * ldb + j * ldj; blocks b = 0..2L are the powers -L..L, b = 2L+1 is P
 cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* coef, float2* coefd, int64_t ldb,
                       int64_t ldj, cudaStream_t s);
-// The same coefficients placed at their stored-block positions: power l at L_max + l,
-// P at 2 L_max + 1 (other positions untouched; the caller clears them).
-cudaError_t fg_coeffs_stored(const double* alpha, int B, int L, int L_max, bool adjoint, float2* coef,
-                             int64_t ldb, int64_t ldj, cudaStream_t s);
 int fg_grad_chunks(int64_t N);
 cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N, float* out, double* partials,
                           cudaStream_t s);
+// Split each signal (row of X) into fp16 planes with a per-signal power-of-two scale.
+// bimag (may be NULL) is cleared first and set nonzero when some signal has a nonzero
+// imaginary part.
 cudaError_t fg_split_signals(const float2* X, int64_t B, int64_t N, int64_t Np, int64_t rows_pad, __half* planes,
-                             int* col_exp, cudaStream_t s);
+                             int* col_exp, cudaStream_t s, int* bimag = nullptr);
+// Split coefficient planes [4][A][Kp] (and per-order exponents) of the fused multi-order
+// assembly: order a's column holds c_l(alpha_a) at stored position L_max + l for |l| <= L,
+// e^{j pi alpha_a} at the P position 2 L_max + 1, zeros elsewhere.
+cudaError_t fg_coeff_planes(const double* alpha, int64_t A, int L, int L_max, int64_t Kp, __half* planes,
+                            int* col_exp, cudaStream_t s);

@@ -19,8 +19,35 @@ __device__ double dsinc_series(double u) {
   return sum;
 }
 
-// coef[b][j] (and coefd[b][j]) for blocks b = 0..2L (power l = b - L) and b = 2L+1 (P):
-//   powers: c_l(a) = sin(pi (a - l)) / (pi (a - l)), c_l'(a);  P: e^{j pi a}, j pi e^{j pi a}.
+// Coefficients of one stored block at order a (sa = sin(pi a), ca = cos(pi a)):
+//   power l: c_l(a) = sin(pi (a - l)) / (pi (a - l)) and c_l'(a) (real);
+//   P (is_p): e^{j pi a} and j pi e^{j pi a}.
+__device__ __forceinline__ void block_coef(double a, double sa, double ca, int l, bool is_p, float2& c, float2& cd) {
+  const double pi = 3.14159265358979323846;
+  if (is_p) {
+    c = make_float2((float)ca, (float)sa);
+    cd = make_float2((float)(-pi * sa), (float)(pi * ca));
+    return;
+  }
+  const double d = a - (double)l;
+  double v, dv;
+  if (d == 0.0) {
+    v = 1.0;
+    dv = 0.0;
+  } else {
+    // sin(pi (a - l)) = (-1)^l sin(pi a), cos(pi (a - l)) = (-1)^l cos(pi a)
+    const double sgn = (l & 1) ? -1.0 : 1.0;
+    v = sgn * sa / (pi * d);
+    if (fabs(d) < 1e-2)
+      dv = pi * dsinc_series(pi * d);
+    else
+      dv = sgn * (pi * d * ca - sa) / (pi * d * d);
+  }
+  c = make_float2((float)v, 0.f);
+  cd = make_float2((float)dv, 0.f);
+}
+
+// coef[b][j] (and coefd[b][j]) for blocks b = 0..2L (power l = b - L) and b = 2L+1 (P).
 // sign = -1 evaluates at -a (the adjoint, Prop. 2).
 // Entry (b, j) is stored at b * ldb + j * ldj.
 // Block b is stored at position b + pos_off for the powers and at p_pos for P.
@@ -31,34 +58,105 @@ __global__ void coeffs_kernel(const double* __restrict__ alpha, int B, int L, do
   const int b = blockIdx.y;
   if (j >= B) return;
   const double a = sign * alpha[j];
-  const double pi = 3.14159265358979323846;
-  const double sa = sinpi(a), ca = cospi(a);
   float2 c, cd;
-  if (b == 2 * L + 1) {
-    c = make_float2((float)ca, (float)sa);
-    cd = make_float2((float)(-pi * sa), (float)(pi * ca));
-  } else {
-    const int l = b - L;
-    const double d = a - (double)l;
-    double v, dv;
-    if (d == 0.0) {
-      v = 1.0;
-      dv = 0.0;
-    } else {
-      // sin(pi (a - l)) = (-1)^l sin(pi a), cos(pi (a - l)) = (-1)^l cos(pi a)
-      const double sgn = (l & 1) ? -1.0 : 1.0;
-      v = sgn * sa / (pi * d);
-      if (fabs(d) < 1e-2)
-        dv = pi * dsinc_series(pi * d);
-      else
-        dv = sgn * (pi * d * ca - sa) / (pi * d * d);
-    }
-    c = make_float2((float)v, 0.f);
-    cd = make_float2((float)dv, 0.f);
-  }
+  block_coef(a, sinpi(a), cospi(a), b - L, b == 2 * L + 1, c, cd);
   const int64_t pos = b == 2 * L + 1 ? p_pos : b + pos_off;
   coef[pos * ldb + (int64_t)j * ldj] = c;
   if (coefd) coefd[pos * ldb + (int64_t)j * ldj] = cd;
+}
+
+// ---------------------------------------------------------------------------------
+// fp16 hi/lo split of a column v (one signal, or one order's coefficient vector):
+// e such that max(|re|, |im|) * 2^e lies in [2^13, 2^14) (0 for an all-zero column), then
+// planes re_hi, re_lo, im_hi, im_lo of v * 2^e with hi = fp16(x), lo = fp16(x - hi).
+__device__ __forceinline__ int split_exponent(float m) {
+  int e = 0;
+  if (m > 0.f && isfinite(m)) {
+    int E;
+    frexpf(m, &E);  // m in [2^(E-1), 2^E)
+    e = (FG_X_TARGET_EXP + 1) - E;
+  }
+  return e;
+}
+
+// Four consecutive entries k0..k0+3 of one column into the four planes (8-byte stores).
+__device__ __forceinline__ void split_store4(const float2 (&v)[4], int e, __half* r_hi, int64_t plane,
+                                             int64_t k0) {
+  __align__(8) __half rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const float re = ldexpf(v[u].x, e), im = ldexpf(v[u].y, e);
+    const __half2 hi = __floats2half2_rn(re, im);
+    const float2 hf = __half22float2(hi);
+    const __half2 lo = __floats2half2_rn(re - hf.x, im - hf.y);
+    rh[u] = __low2half(hi);
+    ih[u] = __high2half(hi);
+    rl[u] = __low2half(lo);
+    il[u] = __high2half(lo);
+  }
+  *reinterpret_cast<uint2*>(r_hi + k0) = *reinterpret_cast<const uint2*>(rh);
+  *reinterpret_cast<uint2*>(r_hi + plane + k0) = *reinterpret_cast<const uint2*>(rl);
+  *reinterpret_cast<uint2*>(r_hi + 2 * plane + k0) = *reinterpret_cast<const uint2*>(ih);
+  *reinterpret_cast<uint2*>(r_hi + 3 * plane + k0) = *reinterpret_cast<const uint2*>(il);
+}
+
+// Block-wide max over 256 threads (every thread gets the result).
+__device__ __forceinline__ float block_max256(float m, float* red) {
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = red[0];
+  for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+  return m;
+}
+
+// Split coefficient planes of the fused multi-order assembly, one CTA per order a:
+// column a holds, at stored-block position q, c_l(alpha_a) for q = L_max + l with
+// |l| <= L, e^{j pi alpha_a} at q = 2 L_max + 1 (P) and zero elsewhere (q < Kp).
+__global__ void __launch_bounds__(256) coeff_planes_kernel(const double* __restrict__ alpha, int L, int L_max,
+                                                           int64_t A, int64_t Kp, __half* __restrict__ planes,
+                                                           int* __restrict__ col_exp) {
+  const int64_t a_idx = blockIdx.x;
+  const double a = alpha[a_idx];
+  const double sa = sinpi(a), ca = cospi(a);
+  auto value = [&](int64_t q) -> float2 {
+    float2 c = make_float2(0.f, 0.f), cd;
+    if (q == 2 * L_max + 1)
+      block_coef(a, sa, ca, 0, true, c, cd);
+    else if (q <= 2 * L_max && q >= L_max - L && q <= L_max + L)
+      block_coef(a, sa, ca, (int)(q - L_max), false, c, cd);
+    return c;
+  };
+  __shared__ float red[8];
+  __half* r_hi = planes + a_idx * Kp;
+  float m = 0.f;
+  if (Kp <= 4 * 256) {  // thread t owns positions 4t..4t+3: each coefficient is evaluated once
+    const int64_t k0 = 4 * (int64_t)threadIdx.x;
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[u] = k0 + u < Kp ? value(k0 + u) : make_float2(0.f, 0.f);
+      m = fmaxf(m, fmaxf(fabsf(v[u].x), fabsf(v[u].y)));
+    }
+    m = block_max256(m, red);
+    const int e = split_exponent(m);
+    if (threadIdx.x == 0) col_exp[a_idx] = e;
+    if (k0 < Kp) split_store4(v, e, r_hi, A * Kp, k0);  // Kp is a multiple of 8
+    return;
+  }
+  for (int64_t q = threadIdx.x; q < Kp; q += blockDim.x) {
+    const float2 c = value(q);
+    m = fmaxf(m, fmaxf(fabsf(c.x), fabsf(c.y)));
+  }
+  m = block_max256(m, red);
+  const int e = split_exponent(m);
+  if (threadIdx.x == 0) col_exp[a_idx] = e;
+  for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < Kp; k0 += 4 * (int64_t)blockDim.x) {
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = value(k0 + u);
+    split_store4(v, e, r_hi, A * Kp, k0);
+  }
 }
 
 constexpr int GR_CHUNK = 4096;
@@ -100,68 +198,73 @@ __global__ void grad_final_kernel(const double* __restrict__ partial, int nchunk
   out[j] = (float)s;
 }
 
-// One CTA per signal column j: e_j such that max(|re|, |im|) * 2^e_j lies in
-// [2^13, 2^14); planes[p][j][k] for p = re_hi, re_lo, im_hi, im_lo of x * 2^e_j.
-// Each thread handles 4 consecutive entries per round (8-byte plane stores); entries
-// k in [N, Np) are written as zeros.
+// One CTA (256 threads) per signal column j: planes[p][j][k] of x_j * 2^{e_j} (see
+// split_exponent); entries k in [N, Np) are written as zeros and rows j in [B, rows_pad)
+// are all zero.  bimag (may be NULL) is set to 1 when the signal has a nonzero (or NaN)
+// imaginary part.
+// G > 0: each thread keeps its G groups of 4 consecutive entries in registers between
+// the max and the split (one read of the column; needs Np <= 1024 G).  G == 0: any Np,
+// the column is read twice.
+template <int G>
 __global__ void __launch_bounds__(256) split_signals_kernel(const float2* __restrict__ X, int64_t B, int64_t N,
                                                             int64_t Np, int64_t rows_pad, __half* __restrict__ planes,
-                                                            int* __restrict__ col_exp) {
+                                                            int* __restrict__ col_exp, int* __restrict__ bimag) {
   const int64_t j = blockIdx.x;
   const int64_t plane = rows_pad * Np;
   __half* r_hi = planes + j * Np;
-  __half* r_lo = r_hi + plane;
-  __half* i_hi = r_hi + 2 * plane;
-  __half* i_lo = r_hi + 3 * plane;
   const float2* x = X + j * N;
   if (j >= B) {  // padding rows are zero
     for (int64_t k = threadIdx.x; k < Np; k += blockDim.x) {
-      r_hi[k] = r_lo[k] = i_hi[k] = i_lo[k] = __float2half(0.f);
+      r_hi[k] = r_hi[plane + k] = r_hi[2 * plane + k] = r_hi[3 * plane + k] = __float2half(0.f);
     }
     return;
   }
-  float m = 0.f;
-  for (int64_t k = threadIdx.x; k < N; k += blockDim.x) {
-    const float2 v = x[k];
-    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-  }
   __shared__ float red[8];
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  m = red[0];
-  for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
-  int e = 0;
-  if (m > 0.f && isfinite(m)) {
-    int E;
-    frexpf(m, &E);  // m in [2^(E-1), 2^E)
-    e = (FG_X_TARGET_EXP + 1) - E;
-  }
-  if (threadIdx.x == 0) col_exp[j] = e;
-  // Np is a multiple of 8, so groups of 4 entries never straddle the row end
-  for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < Np; k0 += 4 * (int64_t)blockDim.x) {
-    __align__(8) __half rh[4], rl[4], ih[4], il[4];
+  float m = 0.f;
+  bool im = false;
+  if constexpr (G > 0) {
+    float2 v[G][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t k = k0 + u;
-      float re = 0.f, im = 0.f;
-      if (k < N) {
-        const float2 v = x[k];
-        re = ldexpf(v.x, e);
-        im = ldexpf(v.y, e);
+    for (int g = 0; g < G; ++g) {
+      const int64_t k0 = 4 * ((int64_t)threadIdx.x + (int64_t)g * blockDim.x);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[g][u] = k0 + u < N ? x[k0 + u] : make_float2(0.f, 0.f);
+        m = fmaxf(m, fmaxf(fabsf(v[g][u].x), fabsf(v[g][u].y)));
+        im |= !(v[g][u].y == 0.f);
       }
-      const __half2 hi = __floats2half2_rn(re, im);
-      const float2 hf = __half22float2(hi);
-      const __half2 lo = __floats2half2_rn(re - hf.x, im - hf.y);
-      rh[u] = __low2half(hi);
-      ih[u] = __high2half(hi);
-      rl[u] = __low2half(lo);
-      il[u] = __high2half(lo);
     }
-    *reinterpret_cast<uint2*>(r_hi + k0) = *reinterpret_cast<const uint2*>(rh);
-    *reinterpret_cast<uint2*>(r_lo + k0) = *reinterpret_cast<const uint2*>(rl);
-    *reinterpret_cast<uint2*>(i_hi + k0) = *reinterpret_cast<const uint2*>(ih);
-    *reinterpret_cast<uint2*>(i_lo + k0) = *reinterpret_cast<const uint2*>(il);
+    const int any_im = __syncthreads_or(im ? 1 : 0);
+    m = block_max256(m, red);
+    const int e = split_exponent(m);
+    if (threadIdx.x == 0) {
+      col_exp[j] = e;
+      if (any_im && bimag) *bimag = 1;  // every writer stores the same value
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int64_t k0 = 4 * ((int64_t)threadIdx.x + (int64_t)g * blockDim.x);
+      if (k0 < Np) split_store4(v[g], e, r_hi, plane, k0);  // Np is a multiple of 8
+    }
+  } else {
+    for (int64_t k = threadIdx.x; k < N; k += blockDim.x) {
+      const float2 v = x[k];
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+      im |= !(v.y == 0.f);
+    }
+    const int any_im = __syncthreads_or(im ? 1 : 0);
+    m = block_max256(m, red);
+    const int e = split_exponent(m);
+    if (threadIdx.x == 0) {
+      col_exp[j] = e;
+      if (any_im && bimag) *bimag = 1;
+    }
+    for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < Np; k0 += 4 * (int64_t)blockDim.x) {
+      float2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = k0 + u < N ? x[k0 + u] : make_float2(0.f, 0.f);
+      split_store4(v, e, r_hi, plane, k0);
+    }
   }
 }
 
@@ -174,17 +277,6 @@ cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* c
   FgTimed timed(FGFRFT_KC_COEFFS, s);
   fg_note_launch(FGFRFT_KC_COEFFS);
   coeffs_kernel<<<grid, 128, 0, s>>>(alpha, B, L, adjoint ? -1.0 : 1.0, coef, coefd, ldb, ldj, 0, 2 * L + 1);
-  return cudaGetLastError();
-}
-
-cudaError_t fg_coeffs_stored(const double* alpha, int B, int L, int L_max, bool adjoint, float2* coef, int64_t ldb,
-                             int64_t ldj, cudaStream_t s) {
-  if (B <= 0) return cudaSuccess;
-  dim3 grid((B + 127) / 128, 2 * L + 2);
-  FgTimed timed(FGFRFT_KC_COEFFS, s);
-  fg_note_launch(FGFRFT_KC_COEFFS);
-  coeffs_kernel<<<grid, 128, 0, s>>>(alpha, B, L, adjoint ? -1.0 : 1.0, coef, nullptr, ldb, ldj, L_max - L,
-                                     2 * L_max + 1);
   return cudaGetLastError();
 }
 
@@ -206,10 +298,32 @@ cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N
 }
 
 cudaError_t fg_split_signals(const float2* X, int64_t B, int64_t N, int64_t Np, int64_t rows_pad, __half* planes,
-                             int* col_exp, cudaStream_t s) {
+                             int* col_exp, cudaStream_t s, int* bimag) {
   if (rows_pad <= 0) return cudaSuccess;
+  if (bimag) {
+    const cudaError_t e = cudaMemsetAsync(bimag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
   FgTimed timed(FGFRFT_KC_SPLIT_SIGNALS, s);
   fg_note_launch(FGFRFT_KC_SPLIT_SIGNALS);
-  split_signals_kernel<<<(unsigned)rows_pad, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp);
+  const unsigned grid = (unsigned)rows_pad;
+  if (Np <= 1024)
+    split_signals_kernel<1><<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
+  else if (Np <= 2048)
+    split_signals_kernel<2><<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
+  else if (Np <= 4096)
+    split_signals_kernel<4><<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
+  else
+    split_signals_kernel<0><<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
+  return cudaGetLastError();
+}
+
+cudaError_t fg_coeff_planes(const double* alpha, int64_t A, int L, int L_max, int64_t Kp, __half* planes,
+                            int* col_exp, cudaStream_t s) {
+  if (A <= 0) return cudaSuccess;
+  if (A > INT32_MAX || Kp < 2 * (int64_t)L_max + 2 || Kp % 8) return cudaErrorInvalidValue;
+  FgTimed timed(FGFRFT_KC_COEFFS, s);
+  fg_note_launch(FGFRFT_KC_COEFFS);
+  coeff_planes_kernel<<<(unsigned)A, 256, 0, s>>>(alpha, L, L_max, A, Kp, planes, col_exp);
   return cudaGetLastError();
 }

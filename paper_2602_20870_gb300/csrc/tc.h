@@ -27,6 +27,7 @@ struct TcGroupedArgs {
   size_t scratch_bytes;
   uint32_t* status;
   bool real_a;             // every Q_g is real (imaginary planes zero): 6 MMAs per k16 step
+  int* bimag;              // work: one word, 0 after the split when every signal is real
 };
 cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s);
 
@@ -49,21 +50,22 @@ struct TcStackedArgs {
   size_t scratch_bytes;
   uint32_t* status;
   bool real_a;             // every stored block is real (real F)
+  int* bimag;              // work: one word, 0 after the split when every signal is real
 };
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s);
 
-// Fused multi-order assembly on the tensor cores: Q_a = sum_k coefT[a][k] S_k over all
-// stored blocks k (zero coefficients outside -L..L), from the entry-major split stack.
+// Fused multi-order assembly on the tensor cores: Q_a = sum_k C[a][k] S_k over all
+// stored blocks k (zero coefficients outside -L..L), from the entry-major split stack and
+// the split coefficient planes Cs (filled by fg_coeff_planes).
 struct TcAssembleArgs {
   const __half* entry_stack;  // [4 planes][entries][Kp] fp16 (scaled by 2^FG_SPLIT_SHIFT)
   int64_t entries;            // N * N
   int64_t K;                  // stored blocks (2 L_max + 2)
   int64_t Kp;                 // row pitch of the entry-major planes (K rounded up to 8)
   int64_t planeT;             // entries per entry-major plane (padded)
-  const float2* coefT;        // [A][K] complex coefficients, order-major
   int64_t A;
-  __half* Cs;                 // work: [4][A][Kp] split coefficients
-  int* col_exp;               // work: [A]
+  const __half* Cs;           // [4][A][Kp] split coefficients
+  const int* col_exp;         // [A] their exponents
   float2* Qc;                 // c64 output [A][N*N] (when Qs is NULL)
   __half* Qs;                 // split output [A][4][plane_elems] or NULL
   int64_t N, Np, plane_elems;
@@ -72,6 +74,7 @@ struct TcAssembleArgs {
   uint32_t* status;
   bool real_a;                // the stored blocks are real (real F)
   bool skip_im;               // split output whose imaginary part is zero (real F, no -1 eigenvalue)
+  bool re_only;               // real blocks and a real result: form only the real accumulator
 };
 cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s);
 size_t fg_tc_assemble_scratch_bytes(int64_t entries, int64_t A);
