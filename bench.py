@@ -534,6 +534,23 @@ def run_precision(args):
     res["assemble_single"] = {"ms": k1 / max(t1, 1), "order_updates_per_s": 1e3 / (k1 / max(t1, 1)),
                               "achieved_gbs": byts / (k1 / max(t1, 1) * 1e-3) / 1e9,
                               "frac_of_hbm": byts / (k1 / max(t1, 1) * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+    # the same order from the half stack (M_0..M_L and P only; M_{-l} read as transposed tiles)
+    Qf = plan.assemble([0.37], L)
+    half = FG.Plan(wl.F, L, storage=FG.STORE_HALF_F16)
+    FG.timing_reset()
+    FG.timing_enable(True)
+    _device_time(lambda: half.assemble([0.37], L), 5, 2)
+    FG.timing_enable(False)
+    n1, t1, k1 = FG.timing_read()["assemble_single"]
+    byts_h = (4.0 if half.real else 8.0) * (L + 1 + (1 if half.r_neg1 > 0 else 0)) * N * N + 8.0 * N * N
+    Qh = half.assemble([0.37], L)
+    res["assemble_single_half"] = {
+        "ms": k1 / max(t1, 1), "order_updates_per_s": 1e3 / (k1 / max(t1, 1)),
+        "achieved_gbs": byts_h / (k1 / max(t1, 1) * 1e-3) / 1e9,
+        "frac_of_hbm": byts_h / (k1 / max(t1, 1) * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
+        "stack_gb": half.plan_bytes / 1e9, "full_stack_gb": plan.plan_bytes / 1e9,
+        "rel_diff_vs_full_storage": float(torch.linalg.norm(Qh - Qf) / torch.linalg.norm(Qf))}
+    del half, Qh, Qf
     line = {"metric": "signals/s and order-updates/s", "workload": wl.name, "unit": "signals/s",
             "value": res["stacked"]["signals_per_s"], "paths": res, "offline_precompute_s": offline_s}
     if not args.no_cpu_baseline:

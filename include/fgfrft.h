@@ -78,6 +78,15 @@ enum fgfrft_storage {
                                  contiguous (row pitch rounded up to 8); lets the fused
                                  multi-order assembly run as one tensor-core GEMM.
                                  Requires FGFRFT_STORE_SPLIT_F16. */
+  FGFRFT_STORE_HALF_F16 = 8,  /* the split fp16 planes of M_0 .. M_{L_max} and P only
+                                 (L_max + 2 blocks, half the split stack): a negative
+                                 power is read as the conjugate transpose of the stored
+                                 positive one, M_{-l} = M_l^H (Prop. 2, as Algorithm 1
+                                 forms it).  Read by the single-order assembly (pairs of
+                                 transposed 64 x 64 tiles, half the bytes), and so by
+                                 fgfrft_assemble and the plain and assembled paths of
+                                 fgfrft_apply; the stacked paths and fgfrft_grad need
+                                 FGFRFT_STORE_SPLIT_F16 or FGFRFT_STORE_C64. */
 };
 
 /* Flags of fgfrft_apply / fgfrft_grad. */
@@ -89,7 +98,12 @@ enum fgfrft_flags {
                                      operators, then one tensor-core GEMM over groups */
   FGFRFT_PATH_STACKED = 0x40,     /* no assembly: the stacked powers [M_-L..M_L, P] as one
                                      tensor-core GEMM against X, per-column orders */
-  FGFRFT_PATH_STACKED_FP32 = 0x80 /* the stacked form on FP32 CUDA cores */
+  FGFRFT_PATH_STACKED_FP32 = 0x80, /* the stacked form on FP32 CUDA cores */
+  FGFRFT_REAL_SIGNALS = 0x100,     /* fgfrft_apply: X_dev holds B x N real float32 signals
+                                      (imaginary parts zero); tensor-core paths only */
+  FGFRFT_REAL_OUTPUT = 0x200       /* fgfrft_apply: Y_dev receives B x N real float32 outputs;
+                                      needs FGFRFT_REAL_SIGNALS, a real F without a -1
+                                      eigenvalue (then Q is real) and the assembled path */
 };
 #define FGFRFT_PATH_MASK 0xF0
 
@@ -104,8 +118,9 @@ int fgfrft_version(void);
 
 /* Bytes of device memory a plan for (N, L_max, storage) occupies: the status
  * word, 2 L_max + 2 blocks of N x N entries (M_{-L_max} .. M_{L_max}, then P)
- * in every storage requested, each block padded to 256 B.  Returns 0 for
- * invalid arguments (N < 1, L_max < 0, no known storage bit, or
+ * in every full storage requested (L_max + 2 blocks M_0 .. M_{L_max}, P for
+ * FGFRFT_STORE_HALF_F16), each storage padded to 256 B.  Returns 0 for invalid
+ * arguments (N < 1, L_max < 0, no storage of the blocks, an unknown bit, or
  * FGFRFT_STORE_ENTRY_F16 without FGFRFT_STORE_SPLIT_F16). */
 size_t fgfrft_plan_bytes(int64_t N, int L_max, int storage);
 
@@ -152,8 +167,9 @@ int fgfrft_plan_info(fgfrft_plan p, int64_t* N, int* L_max, int* storage, int* r
 
 /* Device pointer to stored block l (-L_max <= l <= L_max, or l = L_max + 1 for
  * P) in the given storage (one bit), and the element stride between blocks.
- * For FGFRFT_STORE_C64 the block is N x N c64; for FGFRFT_STORE_SPLIT_F16 it is
- * four consecutive N x N fp16 planes.  NULL if absent. */
+ * For FGFRFT_STORE_C64 the block is N x N c64; for FGFRFT_STORE_SPLIT_F16 and
+ * FGFRFT_STORE_HALF_F16 it is four consecutive fp16 planes of N rows of pitch
+ * round_up(N, 8).  NULL if absent (a negative l in FGFRFT_STORE_HALF_F16). */
 const void* fgfrft_plan_block(fgfrft_plan p, int storage, int l, int64_t* block_stride_elems);
 
 /* Synchronise the stream, read the plan's device status word and clear it:
@@ -179,8 +195,10 @@ size_t fgfrft_work_bytes(fgfrft_plan p, int op, const double* alpha_host, int64_
  * Online part of Algorithm 1 (Def. 1), A orders in one pass over the stack.
  *   alpha_host  A orders.
  *   Q_dev       A x N x N c64 output, Q_dev[a][i][k] = (Q_L^{alpha_a})_{ik}.
- * A = 1 streams the 2L + 2 stored c64 blocks once with bulk-copy staging
- * (needs FGFRFT_STORE_C64).  A > 1 reads each stored entry once for all A
+ * A = 1 streams the stored blocks once: the L + 2 half-stack blocks as pairs
+ * of transposed tiles with FGFRFT_STORE_HALF_F16, else the 2L + 2 c64 blocks
+ * (the two real split planes for a real F) with bulk-copy staging.  A > 1
+ * without an entry-major copy repeats that per order.  A > 1 reads each stored entry once for all A
  * outputs: as one tensor-core GEMM over the entry-major split stack when the plan
  * has FGFRFT_STORE_ENTRY_F16 (split-fp16 products, FP32 accumulation), else on
  * FP32 CUDA cores from the c64 stack.
@@ -197,6 +215,8 @@ int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L,
  * are grouped into runs of equal order; runs of at least 64 columns use
  * FGFRFT_PATH_ASSEMBLED, otherwise FGFRFT_PATH_STACKED (tensor paths need
  * FGFRFT_STORE_SPLIT_F16, else the FP32 paths are used).
+ * FGFRFT_REAL_SIGNALS / FGFRFT_REAL_OUTPUT take real float32 signals / outputs
+ * (half the bytes; FGFRFT_ERR_UNSUPPORTED where their conditions do not hold).
  */
 int fgfrft_apply(fgfrft_plan p, const double* alpha_host, int64_t B, int L,
                  const void* X_dev, void* Y_dev, int flags,

@@ -19,7 +19,7 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 struct Layout {
   int64_t blk_elems, Np, plane_elems, Kp, planeT;
-  size_t off_c64, off_f16, off_f16T, total;
+  size_t off_c64, off_f16, off_f16T, off_h16, total;
 };
 
 Layout plan_layout(int64_t N, int L_max, int storage) {
@@ -37,6 +37,9 @@ Layout plan_layout(int64_t N, int L_max, int storage) {
   l.planeT = round_up(N * N * l.Kp, 128);
   l.off_f16T = off;
   if (storage & FGFRFT_STORE_ENTRY_F16) off = align_up(off + (size_t)4 * l.planeT * sizeof(__half));
+  l.off_h16 = off;
+  if (storage & FGFRFT_STORE_HALF_F16)
+    off = align_up(off + (size_t)(L_max + 2) * 4 * l.plane_elems * sizeof(__half));
   l.total = off;
   return l;
 }
@@ -93,7 +96,10 @@ constexpr int kAssembledMinRun = 64;
 int choose_path(const fgfrft_plan_s* p, const std::vector<double>& a, int flags) {
   int path = flags & FGFRFT_PATH_MASK;
   if (path) return path;
+  if (flags & FGFRFT_REAL_OUTPUT) return FGFRFT_PATH_ASSEMBLED;  // real outputs come from assembled Q
   const bool tensor = (p->storage & FGFRFT_STORE_SPLIT_F16) != 0 && fg_tc_available();
+  if (!p->f16 && !p->c64)  // half stack only: assemble per order group, then Q X
+    return fg_tc_available() ? FGFRFT_PATH_ASSEMBLED : FGFRFT_PATH_PLAIN;
   auto runs = order_runs(a);
   int64_t min_run = INT64_MAX;
   for (auto& r : runs) min_run = std::min(min_run, r.second);
@@ -104,10 +110,26 @@ int choose_path(const fgfrft_plan_s* p, const std::vector<double>& a, int flags)
   return tensor ? FGFRFT_PATH_STACKED : FGFRFT_PATH_STACKED_FP32;
 }
 
+// Path of fgfrft_grad: long runs of one order assemble Q and dQ/dalpha per run (assembled
+// path on the tensor cores, else the plain path); short runs use the stacked form.  A plan
+// with the half stack only always assembles.
+int grad_path(const fgfrft_plan_s* p, const std::vector<double>& a, int flags) {
+  int path = flags & FGFRFT_PATH_MASK;
+  if (path) return path;
+  const bool tc = fg_tc_available();
+  const bool single = p->h16 || p->c64 || (p->real && p->f16);  // single-order kernels available
+  if (!p->f16 && !p->c64) return tc ? FGFRFT_PATH_ASSEMBLED : FGFRFT_PATH_PLAIN;
+  int64_t min_run = INT64_MAX;
+  for (auto& r : order_runs(a)) min_run = std::min(min_run, r.second);
+  if (min_run >= kAssembledMinRun && single) return tc ? FGFRFT_PATH_ASSEMBLED : FGFRFT_PATH_PLAIN;
+  return (p->f16 && tc) ? FGFRFT_PATH_STACKED : FGFRFT_PATH_STACKED_FP32;
+}
+
 // Work layout of fgfrft_assemble (and of the assembly stage of the assembled path).
 struct AssembleWork {
   double* alpha_dev = nullptr;
-  float2* coef = nullptr;    // SIMT: [2L+2][A]; tensor: [A][nblk] order-major, zero outside -L..L
+  float2* coef = nullptr;    // single-order kernels: coefficient tables
+  float2* coefd = nullptr;   // derivative coefficients (dual assembly dQ/dalpha)
   __half* Cs = nullptr;      // tensor: split coefficients [4][A][Kp]
   int* col_exp = nullptr;
   void* scratch = nullptr;
@@ -116,12 +138,13 @@ struct AssembleWork {
   size_t bytes = 0;
 };
 
-AssembleWork carve_assemble(const fgfrft_plan_s* p, char* base, int64_t A, int L) {
+AssembleWork carve_assemble(const fgfrft_plan_s* p, char* base, int64_t A, int L, bool dual = false) {
   AssembleWork w;
   Carve c{base};
-  // one order streams best through the c64 bulk-copy kernel; more orders (or no c64
-  // stack) use the tensor-core GEMM over the entry-major stack
-  w.tensor = p->f16T != nullptr && (A >= 2 || p->c64 == nullptr) && fg_tc_available();
+  // one order streams best through the single-order kernels; more orders (or no c64
+  // stack) use the tensor-core GEMM over the entry-major stack.  The dual assembly
+  // (Q and dQ/dalpha) runs on the single-order kernels.
+  w.tensor = !dual && p->f16T != nullptr && (A >= 2 || p->c64 == nullptr) && fg_tc_available();
   w.alpha_dev = c.take<double>((size_t)A);
   if (w.tensor) {
     w.Cs = c.take<__half>((size_t)4 * A * p->Kp);
@@ -130,6 +153,7 @@ AssembleWork carve_assemble(const fgfrft_plan_s* p, char* base, int64_t A, int L
     w.scratch = c.take<char>(w.scratch_bytes);
   } else {
     w.coef = c.take<float2>((size_t)(2 * L + 2) * A);
+    if (dual) w.coefd = c.take<float2>((size_t)(2 * L + 2) * A);
   }
   w.bytes = c.off;
   return w;
@@ -164,6 +188,18 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
     ta.re_only = p->real && p->r_neg1 == 0;  // real blocks, P = 0: every Q_a is real
     return fg_tc_assemble(ta, s);
   }
+  if (p->h16) {  // half stack: per order, pairs of transposed tiles (half the bytes)
+    cudaError_t e = fg_coeffs(alpha_dev, (int)A, L, false, w.coef, nullptr, 1, 2 * L + 2, s);
+    if (e != cudaSuccess) return e;
+    for (int64_t a = 0; a < A; ++a) {
+      e = fg_assemble_half(p->h16, p->plane_elems, p->L_max, L, !p->real, p->r_neg1 > 0, p->N, p->Np,
+                           w.coef + a * (2 * L + 2), Qc ? Qc + a * p->N * p->N : nullptr,
+                           Qs ? Qs + a * 4 * p->plane_elems : nullptr, p->plane_elems,
+                           !(p->real && p->r_neg1 == 0), p->dstatus, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   cudaError_t e = fg_coeffs(alpha_dev, (int)A, L, false, w.coef, nullptr, A, 1, s);
   if (e != cudaSuccess) return e;
   if (A == 1 && p->real && p->f16)  // one order, real F: stream the two real split planes
@@ -176,6 +212,36 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
                            p->dstatus, s);
 }
 
+// One order on the single-order kernels: coef = [2L+2] (powers at L + l, P at 2L + 1).
+cudaError_t assemble_one(const fgfrft_plan_s* p, const float2* coef, int L, float2* Qc, __half* Qs, cudaStream_t s) {
+  const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
+  if (p->h16)
+    return fg_assemble_half(p->h16, p->plane_elems, p->L_max, L, !p->real, p->r_neg1 > 0, p->N, p->Np, coef, Qc, Qs,
+                            p->plane_elems, !(p->real && p->r_neg1 == 0), p->dstatus, s);
+  if (p->real && p->f16)
+    return fg_assemble_single_real(p->f16, 4 * p->plane_elems, p->plane_elems, b0, nb, pb, p->N, p->Np, coef, Qc, Qs,
+                                   p->plane_elems, p->r_neg1 > 0, p->dstatus, s);
+  if (p->c64)
+    return fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, coef, Qc, p->dstatus, s, Qs, p->N, p->Np,
+                              p->plane_elems);
+  return cudaErrorInvalidValue;
+}
+
+// Q_a and dQ_a/dalpha = sum_l c_l'(a) M_l + j pi e^{j pi a} P (Prop. 3) for A orders, each on
+// the single-order kernels; split outputs Qs, dQs ([A][4][plane_elems]).
+cudaError_t run_assemble_dual(const fgfrft_plan_s* p, const AssembleWork& w, const double* alpha_dev, int64_t A,
+                              int L, __half* Qs, __half* dQs, cudaStream_t s) {
+  cudaError_t e = fg_coeffs(alpha_dev, (int)A, L, false, w.coef, w.coefd, 1, 2 * L + 2, s);
+  if (e != cudaSuccess) return e;
+  for (int64_t a = 0; a < A; ++a) {
+    e = assemble_one(p, w.coef + a * (2 * L + 2), L, nullptr, Qs + a * 4 * p->plane_elems, s);
+    if (e != cudaSuccess) return e;
+    e = assemble_one(p, w.coefd + a * (2 * L + 2), L, nullptr, dQs + a * 4 * p->plane_elems, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Work layout of an apply / grad call; base == nullptr computes the size only.
 struct ApplyWork {
   double* alpha_dev = nullptr;
@@ -184,6 +250,8 @@ struct ApplyWork {
   float2* coefd = nullptr;
   float2* Qc = nullptr;
   __half* Qs = nullptr;
+  float2* dQc = nullptr;  // dual: dQ/dalpha per group (plain path)
+  __half* dQs = nullptr;  // dual: dQ/dalpha per group (assembled path)
   __half* Xs = nullptr;
   int* col_exp = nullptr;
   int* bimag = nullptr;
@@ -197,7 +265,8 @@ struct ApplyWork {
   size_t bytes = 0;
 };
 
-ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int path, int64_t groups, bool grad) {
+ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int path, int64_t groups, bool grad,
+                      bool dual = false) {
   ApplyWork w;
   Carve c{base};
   const int nb = 2 * L + 2;
@@ -208,6 +277,10 @@ ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int 
       w.coef = c.take<float2>((size_t)nb * groups);
       w.Qc = c.take<float2>((size_t)groups * p->N * p->N);
       w.gtab = c.take<int2>((size_t)groups);
+      if (dual) {
+        w.coefd = c.take<float2>((size_t)nb * groups);
+        w.dQc = c.take<float2>((size_t)groups * p->N * p->N);
+      }
       break;
     case FGFRFT_PATH_STACKED_FP32:
       w.coef = c.take<float2>((size_t)nb * B);
@@ -215,16 +288,17 @@ ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int 
       break;
     case FGFRFT_PATH_ASSEMBLED: {
       w.group_alpha_dev = c.take<double>((size_t)groups);
-      w.asm_work = carve_assemble(p, nullptr, groups, L);
+      w.asm_work = carve_assemble(p, nullptr, groups, L, dual);
       w.asm_base = c.take<char>(w.asm_work.bytes);
       w.Qs = c.take<__half>((size_t)groups * 4 * p->plane_elems);
+      if (dual) w.dQs = c.take<__half>((size_t)groups * 4 * p->plane_elems);
       w.xs_rows = fg_tc_signal_rows(B, groups);
       w.Xs = c.take<__half>((size_t)4 * w.xs_rows * p->Np);
       w.col_exp = c.take<int>((size_t)w.xs_rows);
       w.bimag = c.take<int>(1);
       w.tc_scratch_bytes = fg_tc_scratch_bytes(p->N, B, groups, 1);
       w.tc_scratch = c.take<char>(w.tc_scratch_bytes);
-      if (base) w.asm_work = carve_assemble(p, w.asm_base, groups, L);
+      if (base) w.asm_work = carve_assemble(p, w.asm_base, groups, L, dual);
       break;
     }
     case FGFRFT_PATH_STACKED:
@@ -269,8 +343,8 @@ int fgfrft_version(void) { return 100; }
 
 size_t fgfrft_plan_bytes(int64_t N, int L_max, int storage) {
   if (N < 1 || N > 65536 || L_max < 0 || L_max > 1000) return 0;
-  const int known = FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16 | FGFRFT_STORE_ENTRY_F16;
-  if ((storage & (FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16)) == 0) return 0;
+  const int known = FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16 | FGFRFT_STORE_ENTRY_F16 | FGFRFT_STORE_HALF_F16;
+  if ((storage & (FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16 | FGFRFT_STORE_HALF_F16)) == 0) return 0;
   if (storage & ~known) return 0;
   if ((storage & FGFRFT_STORE_ENTRY_F16) && !(storage & FGFRFT_STORE_SPLIT_F16)) return 0;
   return plan_layout(N, L_max, storage).total;
@@ -309,6 +383,7 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   p->c64 = (storage & FGFRFT_STORE_C64) ? (float2*)(pm + lay.off_c64) : nullptr;
   p->f16 = (storage & FGFRFT_STORE_SPLIT_F16) ? (__half*)(pm + lay.off_f16) : nullptr;
   p->f16T = (storage & FGFRFT_STORE_ENTRY_F16) ? (__half*)(pm + lay.off_f16T) : nullptr;
+  p->h16 = (storage & FGFRFT_STORE_HALF_F16) ? (__half*)(pm + lay.off_h16) : nullptr;
   p->Kp = lay.Kp;
   p->planeT = lay.planeT;
 
@@ -400,17 +475,25 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   auto store = [&](int blk, const double2* M, bool conjT) -> bool {
     float2* c = p->c64 ? p->c64 + (int64_t)blk * p->blk_elems : nullptr;
     __half* f = p->f16 ? p->f16 + (int64_t)blk * 4 * p->plane_elems : nullptr;
+    if (!c && !f) return true;
     return fg_store_block(N, M, conjT, c, f, p->Np, p->plane_elems, s) == cudaSuccess;
   };
-  if (!store(blk_of_P(p), Cm, false)) return fail(FGFRFT_ERR_CUDA);
+  // half stack: M_0 .. M_L_max at blocks 0 .. L_max, P at L_max + 1
+  auto store_half = [&](int hb, const double2* M) -> bool {
+    if (!p->h16) return true;
+    return fg_store_block(N, M, false, nullptr, p->h16 + (int64_t)hb * 4 * p->plane_elems, p->Np, p->plane_elems,
+                          s) == cudaSuccess;
+  };
+  if (!store(blk_of_P(p), Cm, false) || !store_half(L_max + 1, Cm)) return fail(FGFRFT_ERR_CUDA);
   if (fg_zaxpby_identity(N, make_double2(-1.0, 0.0), Cm, zero, one, Am, s)) return fail(FGFRFT_ERR_CUDA);
-  if (!store(blk_of_power(p, 0), Am, false)) return fail(FGFRFT_ERR_CUDA);
+  if (!store(blk_of_power(p, 0), Am, false) || !store_half(0, Am)) return fail(FGFRFT_ERR_CUDA);
   double2* cur = Am;
   double2* nxt = Bm;
   for (int k = 1; k <= L_max; ++k) {
     if (fg_zgemm(false, false, n, n, n, one, (const double2*)F_dev, n, cur, n, zero, nxt, n, s))
       return fail(FGFRFT_ERR_CUDA);
-    if (!store(blk_of_power(p, k), nxt, false) || !store(blk_of_power(p, -k), nxt, true)) return fail(FGFRFT_ERR_CUDA);
+    if (!store(blk_of_power(p, k), nxt, false) || !store(blk_of_power(p, -k), nxt, true) || !store_half(k, nxt))
+      return fail(FGFRFT_ERR_CUDA);
     std::swap(cur, nxt);
   }
   if (p->f16T && fg_entry_major(p->f16, p->nblk, N, p->Np, p->plane_elems, p->f16T, p->Kp, p->planeT, s))
@@ -443,6 +526,10 @@ const void* fgfrft_plan_block(fgfrft_plan p, int storage, int l, int64_t* block_
   if (storage == FGFRFT_STORE_SPLIT_F16 && p->f16) {
     if (block_stride_elems) *block_stride_elems = 4 * p->plane_elems;
     return p->f16 + (int64_t)blk * 4 * p->plane_elems;
+  }
+  if (storage == FGFRFT_STORE_HALF_F16 && p->h16 && l >= 0) {
+    if (block_stride_elems) *block_stride_elems = 4 * p->plane_elems;
+    return p->h16 + (int64_t)l * 4 * p->plane_elems;  // l = L_max + 1 is P
   }
   return nullptr;
 }
@@ -482,14 +569,13 @@ size_t fgfrft_work_bytes(fgfrft_plan p, int op, const double* alpha_host, int64_
   if (gather_orders(alpha_host, count, L, flags, a) != FGFRFT_OK) return 0;
   if (flags & FGFRFT_ADJOINT)
     for (auto& v : a) v = -v;
-  int path = op == FGFRFT_OP_GRAD ? ((flags & FGFRFT_PATH_MASK) ? (flags & FGFRFT_PATH_MASK)
-                                                                 : ((p->storage & FGFRFT_STORE_SPLIT_F16) &&
-                                                                            fg_tc_available()
-                                                                        ? FGFRFT_PATH_STACKED
-                                                                        : FGFRFT_PATH_STACKED_FP32))
-                                  : choose_path(p, a, flags);
+  const int path = op == FGFRFT_OP_GRAD ? grad_path(p, a, flags) : choose_path(p, a, flags);
   const int64_t groups = (int64_t)order_runs(a).size();
-  return carve_apply(p, nullptr, count, L, path, groups, op == FGFRFT_OP_GRAD).bytes;
+  if (op == FGFRFT_OP_GRAD) {
+    // the dual forward, the backward at -alpha (the same runs) and the gradient partials
+    return carve_apply(p, nullptr, count, L, path, groups, true, true).bytes;
+  }
+  return carve_apply(p, nullptr, count, L, path, groups, false).bytes;
 }
 
 int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, void* Q_dev, void* work,
@@ -505,17 +591,21 @@ int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, v
     return FGFRFT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   AssembleWork w = carve_assemble(p, (char*)work, A, L);
-  if (!w.tensor && !p->c64) return FGFRFT_ERR_UNSUPPORTED;
+  if (!w.tensor && !p->c64 && !p->h16) return FGFRFT_ERR_UNSUPPORTED;
   CK(fg_h2d(w.alpha_dev, a.data(), (size_t)A * sizeof(double), s));
   CK(run_assemble(p, w, w.alpha_dev, A, L, (float2*)Q_dev, nullptr, s));
   return FGFRFT_OK;
 }
 
 static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, const void* X_dev, void* Y_dev,
-                      void* D_dev, int path, void* work, size_t work_bytes, cudaStream_t s) {
+                      void* D_dev, int path, void* work, size_t work_bytes, cudaStream_t s, int real_io = 0) {
+  const bool x_real = (real_io & FGFRFT_REAL_SIGNALS) != 0, y_real = (real_io & FGFRFT_REAL_OUTPUT) != 0;
+  if ((x_real && path != FGFRFT_PATH_ASSEMBLED && path != FGFRFT_PATH_STACKED) ||
+      (y_real && (!x_real || path != FGFRFT_PATH_ASSEMBLED || !p->real || p->r_neg1 != 0 || D_dev)))
+    return FGFRFT_ERR_UNSUPPORTED;
   const auto runs = order_runs(a);
   const int64_t groups = (int64_t)runs.size();
-  ApplyWork w = carve_apply(p, (char*)work, B, L, path, groups, false);
+  ApplyWork w = carve_apply(p, (char*)work, B, L, path, groups, false, D_dev != nullptr);
   if (work_bytes < w.bytes) return FGFRFT_ERR_INVALID_ARG;
   const int n = (int)p->N;
   const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
@@ -523,26 +613,21 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
   float2* Y = (float2*)Y_dev;
   switch (path) {
     case FGFRFT_PATH_PLAIN: {
-      if (!p->c64 && !(p->real && p->f16)) return FGFRFT_ERR_UNSUPPORTED;
+      if (!p->c64 && !(p->real && p->f16) && !p->h16) return FGFRFT_ERR_UNSUPPORTED;
       if (groups > 65535) return FGFRFT_ERR_UNSUPPORTED;
       std::vector<double> ga((size_t)groups);
       for (int64_t g = 0; g < groups; ++g) ga[(size_t)g] = a[(size_t)runs[(size_t)g].first];
       CK(fg_h2d(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), s));
-      // coefficient vectors one per order, contiguous: [groups][2L+2]
-      CK(fg_coeffs(w.group_alpha_dev, (int)groups, L, false, w.coef, nullptr, 1, nb + 1, s));
+      // coefficient vectors one per order, contiguous: [groups][2L+2] (and c_l' for the dual)
+      CK(fg_coeffs(w.group_alpha_dev, (int)groups, L, false, w.coef, D_dev ? w.coefd : nullptr, 1, nb + 1, s));
       // per order: stream the stack once into Q_g (one single-order assembly launch each;
       // real F streams the two real split planes), then all Q_g X_g on FP32 CUDA cores in
       // one batched launch
       std::vector<int2> gt((size_t)groups);
       int maxc = 0;
       for (int64_t g = 0; g < groups; ++g) {
-        float2* Qg = w.Qc + g * p->N * p->N;
-        if (p->real && p->f16)
-          CK(fg_assemble_single_real(p->f16, 4 * p->plane_elems, p->plane_elems, b0, nb, pb, p->N, p->Np,
-                                     w.coef + g * (nb + 1), Qg, nullptr, 0, true, p->dstatus, s));
-        else
-          CK(fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, w.coef + g * (nb + 1), Qg,
-                                p->dstatus, s));
+        CK(assemble_one(p, w.coef + g * (nb + 1), L, w.Qc + g * p->N * p->N, nullptr, s));
+        if (D_dev) CK(assemble_one(p, w.coefd + g * (nb + 1), L, w.dQc + g * p->N * p->N, nullptr, s));
         gt[(size_t)g] = make_int2((int)runs[(size_t)g].first, (int)runs[(size_t)g].second);
         maxc = std::max(maxc, (int)runs[(size_t)g].second);
       }
@@ -561,7 +646,12 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       sa.group_stride = p->N * p->N;
       sa.max_group_cols = maxc;
       sa.ngroups = (int)groups;
-      CK(fg_simt_stacked(sa, s));
+      if (Y) CK(fg_simt_stacked(sa, s));
+      if (D_dev) {  // D = (dQ/dalpha) X
+        sa.A = w.dQc;
+        sa.Y = (float2*)D_dev;
+        CK(fg_simt_stacked(sa, s));
+      }
       return FGFRFT_OK;
     }
     case FGFRFT_PATH_STACKED_FP32: {
@@ -591,7 +681,9 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       return FGFRFT_OK;
     }
     case FGFRFT_PATH_ASSEMBLED: {
-      if (!fg_tc_available() || !p->f16 || (!p->c64 && !p->f16T)) return FGFRFT_ERR_UNSUPPORTED;
+      if (!fg_tc_available()) return FGFRFT_ERR_UNSUPPORTED;
+      if (D_dev ? !(p->h16 || p->c64 || (p->real && p->f16)) : !(p->h16 || (p->f16 && (p->c64 || p->f16T))))
+        return FGFRFT_ERR_UNSUPPORTED;
       std::vector<double> ga((size_t)groups);
       std::vector<int64_t> gstart((size_t)groups), gcount((size_t)groups);
       for (int64_t g = 0; g < groups; ++g) {
@@ -599,9 +691,19 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
         gstart[(size_t)g] = runs[(size_t)g].first;
         gcount[(size_t)g] = runs[(size_t)g].second;
       }
+      // every host table of the call goes up first, so no copy waits in the middle of the call
+      std::vector<int4> tiles;
+      fg_tc_grouped_tiles(p->N, groups, gstart.data(), gcount.data(), tiles);
+      if (tiles.size() * sizeof(int4) > w.tc_scratch_bytes) return FGFRFT_ERR_INVALID_ARG;
       CK(fg_h2d(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), s));
-      CK(run_assemble(p, w.asm_work, w.group_alpha_dev, groups, L, nullptr, w.Qs, s));
+      CK(fg_h2d(w.tc_scratch, tiles.data(), tiles.size() * sizeof(int4), s));
+      if (D_dev)
+        CK(run_assemble_dual(p, w.asm_work, w.group_alpha_dev, groups, L, w.Qs, w.dQs, s));
+      else
+        CK(run_assemble(p, w.asm_work, w.group_alpha_dev, groups, L, nullptr, w.Qs, s));
       TcGroupedArgs ta{};
+      ta.tiles_dev = (const int4*)w.tc_scratch;
+      ta.ntiles = (int64_t)tiles.size();
       ta.N = p->N;
       ta.Np = p->Np;
       ta.plane_elems = p->plane_elems;
@@ -620,7 +722,15 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       ta.status = p->dstatus;
       ta.real_a = p->real && p->r_neg1 == 0;  // Q = R + j sin(pi a) P is real when P = 0
       ta.bimag = w.bimag;
-      CK(fg_tc_grouped_apply(ta, s));
+      ta.x_real = x_real;
+      ta.y_real = y_real;
+      if (Y) CK(fg_tc_grouped_apply(ta, s));
+      if (D_dev) {  // D = (dQ/dalpha) X on the same split signals
+        ta.Qs = w.dQs;
+        ta.Y = (float2*)D_dev;
+        ta.x_split_done = Y != nullptr;
+        CK(fg_tc_grouped_apply(ta, s));
+      }
       return FGFRFT_OK;
     }
     case FGFRFT_PATH_STACKED: {
@@ -649,6 +759,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       ta.status = p->dstatus;
       ta.real_a = p->real;
       ta.bimag = w.bimag;
+      ta.x_real = x_real;
       CK(fg_tc_stacked_apply(ta, s));
       return FGFRFT_OK;
     }
@@ -661,15 +772,18 @@ int fgfrft_apply(fgfrft_plan p, const double* alpha_host, int64_t B, int L, cons
                  int flags, void* work, size_t work_bytes, void* stream) {
   if (!p || !alpha_host || B < 1 || !X_dev || !Y_dev || !work || L < 0) return FGFRFT_ERR_INVALID_ARG;
   if (L > p->L_max) return FGFRFT_ERR_UNSUPPORTED;
-  if (!aligned(work) || !aligned(X_dev, 8) || !aligned(Y_dev, 8)) return FGFRFT_ERR_INVALID_ARG;
+  const int real_io = flags & (FGFRFT_REAL_SIGNALS | FGFRFT_REAL_OUTPUT);
+  if (!aligned(work) || !aligned(X_dev, (real_io & FGFRFT_REAL_SIGNALS) ? 4 : 8) ||
+      !aligned(Y_dev, (real_io & FGFRFT_REAL_OUTPUT) ? 4 : 8))
+    return FGFRFT_ERR_INVALID_ARG;
   std::vector<double> a;
   int rc = gather_orders(alpha_host, B, L, flags, a);
   if (rc) return rc;
   if (flags & FGFRFT_ADJOINT)
     for (auto& v : a) v = -v;
   const int path = choose_path(p, a, flags);
-  if (path == FGFRFT_PATH_PLAIN && !p->c64) return FGFRFT_ERR_UNSUPPORTED;
-  return apply_impl(p, a, B, L, X_dev, Y_dev, nullptr, path, work, work_bytes, (cudaStream_t)stream);
+  if (path == FGFRFT_PATH_PLAIN && !p->c64 && !(p->real && p->f16) && !p->h16) return FGFRFT_ERR_UNSUPPORTED;
+  return apply_impl(p, a, B, L, X_dev, Y_dev, nullptr, path, work, work_bytes, (cudaStream_t)stream, real_io);
 }
 
 int fgfrft_grad(fgfrft_plan p, const double* alpha_host, int64_t B, int L, const void* X_dev, void* Y_dev,
@@ -685,11 +799,9 @@ int fgfrft_grad(fgfrft_plan p, const double* alpha_host, int64_t B, int L, const
   std::vector<double> a;
   int rc = gather_orders(alpha_host, B, L, flags & ~FGFRFT_ADJOINT, a);
   if (rc) return rc;
-  int path = flags & FGFRFT_PATH_MASK;
-  if (!path)
-    path = (p->f16 && fg_tc_available()) ? FGFRFT_PATH_STACKED : FGFRFT_PATH_STACKED_FP32;
-  if (path != FGFRFT_PATH_STACKED && path != FGFRFT_PATH_STACKED_FP32) return FGFRFT_ERR_UNSUPPORTED;
-  ApplyWork w = carve_apply(p, (char*)work, B, L, path, 1, true);
+  const int path = grad_path(p, a, flags);
+  const int64_t groups = (int64_t)order_runs(a).size();
+  ApplyWork w = carve_apply(p, (char*)work, B, L, path, groups, true, true);
   if (work_bytes < w.bytes) return FGFRFT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (X_dev) {

@@ -93,6 +93,8 @@ struct TcParams {
   int skip_im;        // split output: the imaginary planes are zero and not written
   int re_only;        // real A and a real product: only the real accumulator is formed
   int smem_bytes;     // dynamic shared memory usable from the 1024-aligned base
+  float uscale;       // nonzero: every column has this output scale (no per-column exponents)
+  int y_real;         // grouped output: Y is real float32 (only the real parts are written)
   const int* bimag;   // NULL, or a device word that is 0 when every B column is real
   const float2* coef;
   const float2* coefd;
@@ -128,15 +130,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void fence_tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -169,6 +162,34 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, Smem& sm
 
 __device__ __forceinline__ int4 tile_of(const TcParams& p, int t) {
   return p.tiles ? p.tiles[t] : make_int4(t, 0, 0, p.arith_cols);
+}
+
+// Split-output epilogue of one 32-column chunk: column j0 + c of this thread's row goes to
+// Qs + (j0 + c) * 4 * qplane + qoff as fp16 hi/lo planes (re_hi, re_lo, im_hi, im_lo).
+// UNIFORM: every column has the scale p.uscale (no per-column table).
+template <bool UNIFORM>
+__device__ __forceinline__ void split_out_cols(const uint32_t (&vr)[32], const uint32_t (&vi)[32], const TcParams& p,
+                                               const float* scale, int cc, int j0, int ncol, int64_t qoff) {
+  const int64_t pl = p.qplane, cs = 4 * pl;
+  __half* qp = p.Qs + (int64_t)j0 * cs + qoff;
+  const bool write_im = !p.skip_im;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    if (c < ncol) {
+      const float sc = UNIFORM ? p.uscale : scale[cc * 32 + c];
+      const float re = __uint_as_float(vr[c]) * sc, im = __uint_as_float(vi[c]) * sc;
+      const __half2 hi = __floats2half2_rn(re, im);
+      const float2 hf = __half22float2(hi);
+      const __half2 lo = __floats2half2_rn(re - hf.x, im - hf.y);
+      qp[0] = __low2half(hi);
+      qp[pl] = __low2half(lo);
+      if (write_im) {
+        qp[2 * pl] = __high2half(hi);
+        qp[3 * pl] = __high2half(lo);
+      }
+    }
+    qp += cs;
+  }
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory"); }
@@ -230,7 +251,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      uint32_t kit = 0;
+      int s_cur = 0;  // ring position and phase of the next stage
+      uint32_t ph_cur = 0;
       uint32_t issued[TC_MAXST] = {};
       bool ok = true;
       int4 next = blockIdx.x < p.ntiles ? tile_of(p, blockIdx.x) : make_int4(0, 0, 0, 0);
@@ -247,9 +269,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (t + (int)gridDim.x < p.ntiles) next = tile_of(p, t + gridDim.x);  // prefetch
         for (int b = 0; ok && b < p.nblk; ++b) {
           const int zA = p.grouped ? tile.y : 4 * (b < p.nb_pow ? p.b0 + b : p.p_blk);
-          for (int kc = 0; kc < p.kchunks; ++kc, ++kit) {
-            const int s = (int)(kit % nst);
-            const uint32_t ph = (kit / nst) & 1;
+          for (int kc = 0; kc < p.kchunks; ++kc) {
+            const int s = s_cur;
+            const uint32_t ph = ph_cur;
+            if (++s_cur == nst) {
+              s_cur = 0;
+              ph_cur ^= 1u;
+            }
             if (!tc_wait(&sm.empty[s], ph ^ 1, sm, p.status)) {
               ok = false;
               break;
@@ -286,7 +312,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      uint32_t kit = 0, bc = 0;
+      int s_cur = 0;
+      uint32_t ph_cur = 0, bc = 0;
       bool ok = true;
       if (RB && blockIdx.x < p.ntiles) ok = tc_wait(&sm.bfull, 0, sm, p.status);
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
@@ -299,9 +326,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           fence_tc_after();
           const uint32_t d_re = tmem + buf * (2 * TC_BN);
           const uint32_t d_im = d_re + TC_BN;
-          for (int kc = 0; kc < p.kchunks; ++kc, ++kit) {
-            const int s = (int)(kit % nst);
-            const uint32_t ph = (kit / nst) & 1;
+          for (int kc = 0; kc < p.kchunks; ++kc) {
+            const int s = s_cur;
+            const uint32_t ph = ph_cur;
+            if (++s_cur == nst) {
+              s_cur = 0;
+              ph_cur ^= 1u;
+            }
             if (!tc_wait(&sm.full[s], ph, sm, p.status)) {
               ok = false;
               break;
@@ -384,9 +415,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         next = tile_of(p, t + gridDim.x);
         next_scale = col_scale(next);
       }
-      epi_bar();
-      if (et < TC_BN) sm.scale[et] = my_scale;
-      epi_bar();
+      if (p.uscale == 0.f) {  // per-column scales: publish this tile's table
+        epi_bar();
+        if (et < TC_BN) sm.scale[et] = my_scale;
+        epi_bar();
+      }
       const int64_t gi = (int64_t)tile.x * TC_BM + row;
       const bool row_ok = gi < p.rows;
       int64_t qoff = 0;
@@ -394,6 +427,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int64_t qi = gi / p.qN;
         qoff = qi * p.qNp + (gi - qi * p.qN);
       }
+
       for (int b = 0; b < p.nblk; ++b, ++bc) {
         const uint32_t buf = bc & 1, tph = (bc >> 1) & 1;
         if (!tc_wait(&sm.tfull[buf], tph, sm, p.status)) {
@@ -421,31 +455,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // rows past the end: nothing to store
           } else if (split_out) {
             // value * 2^FG_SPLIT_SHIFT as fp16 hi + lo, four planes per column
-            const int64_t pl = p.qplane;
-            __half* qp = p.Qs + (int64_t)j0 * 4 * pl + qoff;
+            if (p.uscale != 0.f)
+              split_out_cols<true>(vr, vi, p, sm.scale, cc, j0, ncol, qoff);
+            else
+              split_out_cols<false>(vr, vi, p, sm.scale, cc, j0, ncol, qoff);
+          } else if (p.coef == nullptr && p.y_real) {
+            float* yp = reinterpret_cast<float*>(p.Y) + (int64_t)j0 * p.rows + gi;
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
-              if (c < ncol) {
-                const float sc = sm.scale[cc * 32 + c];
-                const float re = __uint_as_float(vr[c]) * sc, im = __uint_as_float(vi[c]) * sc;
-                const __half2 hi = __floats2half2_rn(re, im);
-                const float2 hf = __half22float2(hi);
-                const __half2 lo = __floats2half2_rn(re - hf.x, im - hf.y);
-                qp[0] = __low2half(hi);
-                qp[pl] = __low2half(lo);
-                if (!p.skip_im) {
-                  qp[2 * pl] = __high2half(hi);
-                  qp[3 * pl] = __high2half(lo);
-                }
-              }
-              qp += 4 * pl;
+              if (c < ncol) *yp = __uint_as_float(vr[c]) * sm.scale[cc * 32 + c];
+              yp += p.rows;
             }
           } else if (p.coef == nullptr) {
             float2* yp = p.Y + (int64_t)j0 * p.rows + gi;
+            const bool uni = p.uscale != 0.f;
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
               if (c < ncol) {
-                const float sc = sm.scale[cc * 32 + c];
+                const float sc = uni ? p.uscale : sm.scale[cc * 32 + c];
                 *yp = make_float2(__uint_as_float(vr[c]) * sc, __uint_as_float(vi[c]) * sc);
               }
               yp += p.rows;
@@ -514,19 +541,33 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3-D fp16 map: dim0 = k (N, contiguous), dim1 = rows (pitch Np), dim2 = planes (stride plane_elems).
+// 3-D fp16 map: dim0 = k (N, contiguous), dim1 = rows (pitch Np), dim2 = planes (stride plane_elems);
+// 32 k x box_rows boxes, 64-byte swizzle (the MMA operand layout).
 bool make_map(CUtensorMap* m, const void* base, int64_t N, int64_t rows, int64_t Np, int64_t nplanes,
               int64_t plane_elems, int box_rows) {
+  return fg_make_map_f16(m, base, N, rows, Np, nplanes, plane_elems, TC_KC, box_rows, 64);
+}
+
+}  // namespace
+
+bool fg_make_map_f16(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int64_t pitch, int64_t nplanes,
+                     int64_t plane_elems, int box_cols, int box_rows, int swizzle_bytes) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)rows, (cuuint64_t)nplanes};
-  cuuint64_t strides[2] = {(cuuint64_t)Np * 2, (cuuint64_t)plane_elems * 2};
-  cuuint32_t box[3] = {(cuuint32_t)TC_KC, (cuuint32_t)box_rows, 1};
+  const CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                                      : CU_TENSOR_MAP_SWIZZLE_NONE;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)nplanes};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch * 2, (cuuint64_t)plane_elems * 2};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+namespace {
 
 int smem_optin() {
   static int n = 0;
@@ -577,8 +618,8 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vect
                    void* scratch, size_t scratch_bytes, cudaStream_t s, int kclass = FGFRFT_KC_TC_GEMM,
                    int bn = 128, bool resident_b = false, bool real_a = false) {
   if (tiles.empty()) {
-    if (p.ntiles <= 0 || p.arith_cols <= 0) return cudaSuccess;  // arithmetic tiles (no table)
-    p.tiles = nullptr;
+    // a table already on the device (p.tiles), or arithmetic tiles (p.tiles == NULL)
+    if (p.ntiles <= 0 || (!p.tiles && p.arith_cols <= 0)) return cudaSuccess;
   } else {
     const size_t tbytes = tiles.size() * sizeof(int4);
     if (tbytes > scratch_bytes) return cudaErrorInvalidValue;
@@ -622,23 +663,36 @@ size_t fg_tc_scratch_bytes(int64_t N, int64_t B, int64_t groups, int) {
   return (size_t)(row_tiles * col_tiles) * sizeof(int4) + 256;
 }
 
+void fg_tc_grouped_tiles(int64_t N, int64_t groups, const int64_t* gstart, const int64_t* gcount,
+                         std::vector<int4>& tiles) {
+  tiles.clear();
+  const int row_tiles = (int)((N + TC_BM - 1) / TC_BM);
+  for (int64_t g = 0; g < groups; ++g) {
+    const int64_t c0 = gstart[g], c1 = gstart[g] + gcount[g];
+    for (int rt = 0; rt < row_tiles; ++rt)
+      for (int64_t c = c0; c < c1; c += TC_BN_MAX)
+        tiles.push_back(make_int4(rt, (int)(4 * g), (int)c, (int)std::min<int64_t>(c + TC_BN_MAX, c1)));
+  }
+}
+
 cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   if (a.N > (1 << 24) || a.B > (1 << 30)) return cudaErrorInvalidValue;
-  cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s, a.bimag);
-  if (e != cudaSuccess) return e;
+  if (!a.x_split_done) {
+    cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s, a.bimag, a.x_real);
+    if (e != cudaSuccess) return e;
+  }
   CUtensorMap mA, mB;
   if (!make_map(&mA, a.Qs, a.N, a.N, a.Np, 4 * a.groups, a.plane_elems, TC_BM) ||
       !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN_MAX))
     return cudaErrorInvalidValue;
   std::vector<int4> tiles;
-  const int row_tiles = (int)((a.N + TC_BM - 1) / TC_BM);
-  for (int64_t g = 0; g < a.groups; ++g) {
-    const int64_t c0 = a.gstart[g], c1 = a.gstart[g] + a.gcount[g];
-    for (int rt = 0; rt < row_tiles; ++rt)
-      for (int64_t c = c0; c < c1; c += TC_BN_MAX)
-        tiles.push_back(make_int4(rt, (int)(4 * g), (int)c, (int)std::min<int64_t>(c + TC_BN_MAX, c1)));
-  }
   TcParams p{};
+  if (a.tiles_dev) {  // uploaded by the caller at the start of the call
+    p.tiles = a.tiles_dev;
+    p.ntiles = (int)a.ntiles;
+  } else {
+    fg_tc_grouped_tiles(a.N, a.groups, a.gstart, a.gcount, tiles);
+  }
   p.nblk = 1;
   p.grouped = 1;
   p.rows = a.N;
@@ -647,12 +701,13 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   p.col_exp = a.col_exp;
   p.status = a.status;
   p.bimag = a.bimag;
+  p.y_real = a.y_real ? 1 : 0;
   return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, 128, false, a.real_a);
 }
 
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   if (a.N > (1 << 24) || a.B > (1 << 30)) return cudaErrorInvalidValue;
-  cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s, a.bimag);
+  cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s, a.bimag, a.x_real);
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
   const int64_t nplanes = 4 * (int64_t)(std::max(a.b0 + a.nb_pow, a.p_blk + 1));
@@ -718,6 +773,8 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   p.status = a.status;
   p.skip_im = a.skip_im ? 1 : 0;
   p.re_only = a.re_only && a.real_a ? 1 : 0;
+  // one exponent for every coefficient column (FG_COEF_EXP)
+  p.uscale = ldexpf(1.0f, a.Qs ? -FG_COEF_EXP : -(FG_SPLIT_SHIFT + FG_COEF_EXP));
   // one column tile (A <= 64): the coefficient operand stays resident in shared memory
   const bool rb = bn == 64 && p.kchunks <= TC_RB_MAXCH;
   return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, bn, rb, a.real_a);

@@ -1,6 +1,7 @@
 // Internal declarations shared by the libfgfrft translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -23,6 +24,7 @@ struct fgfrft_plan_s {
   float2* c64;         // [nblk][blk_elems] or NULL
   __half* f16;         // [nblk][4][plane_elems] or NULL; planes re_hi, re_lo, im_hi, im_lo
   __half* f16T;        // entry-major copy [4][N*N][Kp] or NULL (fused multi-order assembly)
+  __half* h16;         // half stack [L_max + 2][4][plane_elems]: M_0 .. M_L_max, then P; or NULL
   int64_t Kp;          // entry-major row pitch (nblk rounded up to 8)
   int64_t planeT;      // entries per entry-major plane (padded to 128)
   int r_neg1;
@@ -42,6 +44,8 @@ static inline int blk_of_P(const fgfrft_plan_s* p) { return 2 * p->L_max + 1; }
 #define FG_SPLIT_SHIFT 12
 // Signals are scaled per column by 2^e so that max |x| * 2^e lies in [2^13, 2^14).
 #define FG_X_TARGET_EXP 13
+// The fused assembly's coefficients (modulus at most 1) are all scaled by 2^FG_COEF_EXP.
+#define FG_COEF_EXP 14
 
 // Device status codes (OR-ed into the plan's status word).
 #define FG_STATUS_WAIT_TIMEOUT 1u
@@ -135,6 +139,16 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   return p;
 }
 
+// 3-D tensor-map tile load (global -> shared), completion counted in bytes on *bar.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -150,6 +164,12 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
 // instrumentation (timing.cu): per-class launch counters and optional event timing
 // ---------------------------------------------------------------------------
 void fg_note_launch(int cls, int n = 1);
+
+// 3-D fp16 tensor map {cols (contiguous), rows (pitch elements apart), planes (plane_elems
+// apart)} with a box_cols x box_rows x 1 box; swizzle_bytes is 0, 32, 64 or 128.  Out-of-range
+// elements of a box read as zero.  False if the driver rejects the map.
+bool fg_make_map_f16(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int64_t pitch, int64_t nplanes,
+                     int64_t plane_elems, int box_cols, int box_rows, int swizzle_bytes);
 
 // Host-to-device copy of a small per-call table, staged through pinned memory so that the
 // call stays asynchronous (the source may be reused as soon as this returns).
@@ -184,6 +204,12 @@ cudaError_t fg_entry_major(const __half* f16, int nblk, int64_t N, int64_t Np, i
                            int64_t Kp, int64_t planeT, cudaStream_t s);
 
 // assemble.cu
+// One order from the half stack (blocks M_0..M_L_max and P, split fp16 planes): Q = e^{j pi a} P
+// + sum_{|l| <= L} c_l M_l with M_{-l} = M_l^H read as transposed tiles.  coef = [2L+2] as
+// fg_coeffs writes it.  c64 output Q [N][N] or split output Qs (pitch Np, plane stride q_plane).
+cudaError_t fg_assemble_half(const __half* planes, int64_t plane_elems, int L_max, int L, bool cplx, bool has_p,
+                             int64_t N, int64_t Np, const float2* coef, float2* Q, __half* Qs, int64_t q_plane,
+                             bool write_im, uint32_t* status, cudaStream_t s);
 // Q (c64, [NN]) or, with Qs != NULL, split fp16 planes of N rows x Np (plane stride plane_elems).
 cudaError_t fg_assemble_single(const float2* stack, int64_t blk_elems, int b0, int nb_pow, int p_blk,
                                int64_t NN, const float2* coef, float2* Q, uint32_t* status, cudaStream_t s,
@@ -231,9 +257,9 @@ cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N
                           cudaStream_t s);
 // Split each signal (row of X) into fp16 planes with a per-signal power-of-two scale.
 // bimag (may be NULL) is cleared first and set nonzero when some signal has a nonzero
-// imaginary part.
-cudaError_t fg_split_signals(const float2* X, int64_t B, int64_t N, int64_t Np, int64_t rows_pad, __half* planes,
-                             int* col_exp, cudaStream_t s, int* bimag = nullptr);
+// imaginary part.  X is B x N c64, or B x N real float32 when x_real.
+cudaError_t fg_split_signals(const void* X, int64_t B, int64_t N, int64_t Np, int64_t rows_pad, __half* planes,
+                             int* col_exp, cudaStream_t s, int* bimag = nullptr, bool x_real = false);
 // Split coefficient planes [4][A][Kp] (and per-order exponents) of the fused multi-order
 // assembly: order a's column holds c_l(alpha_a) at stored position L_max + l for |l| <= L,
 // e^{j pi alpha_a} at the P position 2 L_max + 1, zeros elsewhere.

@@ -51,15 +51,25 @@ __device__ __forceinline__ void block_coef(double a, double sa, double ca, int l
 // sign = -1 evaluates at -a (the adjoint, Prop. 2).
 // Entry (b, j) is stored at b * ldb + j * ldj.
 // Block b is stored at position b + pos_off for the powers and at p_pos for P.
-__global__ void coeffs_kernel(const double* __restrict__ alpha, int B, int L, double sign,
-                              float2* __restrict__ coef, float2* __restrict__ coefd, int64_t ldb, int64_t ldj,
-                              int pos_off, int p_pos) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y;
-  if (j >= B) return;
-  const double a = sign * alpha[j];
+// A CTA covers 32 columns x 8 blocks; sin(pi a) and cos(pi a) are evaluated once per column
+// (FP64 is a slow pipe on this part).
+__global__ void __launch_bounds__(256) coeffs_kernel(const double* __restrict__ alpha, int B, int L, double sign,
+                                                     float2* __restrict__ coef, float2* __restrict__ coefd,
+                                                     int64_t ldb, int64_t ldj, int pos_off, int p_pos) {
+  __shared__ double s_a[32], s_sa[32], s_ca[32];
+  const int jl = threadIdx.x & 31, bl = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + jl;
+  if (bl == 0 && j < B) {
+    const double a = sign * alpha[j];
+    s_a[jl] = a;
+    s_sa[jl] = sinpi(a);
+    s_ca[jl] = cospi(a);
+  }
+  __syncthreads();
+  const int b = blockIdx.y * 8 + bl;
+  if (j >= B || b > 2 * L + 1) return;
   float2 c, cd;
-  block_coef(a, sinpi(a), cospi(a), b - L, b == 2 * L + 1, c, cd);
+  block_coef(s_a[jl], s_sa[jl], s_ca[jl], b - L, b == 2 * L + 1, c, cd);
   const int64_t pos = b == 2 * L + 1 ? p_pos : b + pos_off;
   coef[pos * ldb + (int64_t)j * ldj] = c;
   if (coefd) coefd[pos * ldb + (int64_t)j * ldj] = cd;
@@ -112,50 +122,36 @@ __device__ __forceinline__ float block_max256(float m, float* red) {
 
 // Split coefficient planes of the fused multi-order assembly, one CTA per order a:
 // column a holds, at stored-block position q, c_l(alpha_a) for q = L_max + l with
-// |l| <= L, e^{j pi alpha_a} at q = 2 L_max + 1 (P) and zero elsewhere (q < Kp).
+// |l| <= L, e^{j pi alpha_a} at q = 2 L_max + 1 (P) and zero elsewhere (q < Kp).  Every
+// coefficient has modulus at most 1, so all columns share the exponent FG_COEF_EXP
+// (values at most 2^14 in fp16).
 __global__ void __launch_bounds__(256) coeff_planes_kernel(const double* __restrict__ alpha, int L, int L_max,
                                                            int64_t A, int64_t Kp, __half* __restrict__ planes,
                                                            int* __restrict__ col_exp) {
   const int64_t a_idx = blockIdx.x;
+  __shared__ double s_sc[2];
+  if (threadIdx.x == 0) {  // once per order: FP64 is a slow pipe on this part
+    s_sc[0] = sinpi(alpha[a_idx]);
+    s_sc[1] = cospi(alpha[a_idx]);
+    col_exp[a_idx] = FG_COEF_EXP;
+  }
+  __syncthreads();
   const double a = alpha[a_idx];
-  const double sa = sinpi(a), ca = cospi(a);
-  auto value = [&](int64_t q) -> float2 {
-    float2 c = make_float2(0.f, 0.f), cd;
-    if (q == 2 * L_max + 1)
-      block_coef(a, sa, ca, 0, true, c, cd);
-    else if (q <= 2 * L_max && q >= L_max - L && q <= L_max + L)
-      block_coef(a, sa, ca, (int)(q - L_max), false, c, cd);
-    return c;
-  };
-  __shared__ float red[8];
+  const double sa = s_sc[0], ca = s_sc[1];
   __half* r_hi = planes + a_idx * Kp;
-  float m = 0.f;
-  if (Kp <= 4 * 256) {  // thread t owns positions 4t..4t+3: each coefficient is evaluated once
-    const int64_t k0 = 4 * (int64_t)threadIdx.x;
-    float2 v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      v[u] = k0 + u < Kp ? value(k0 + u) : make_float2(0.f, 0.f);
-      m = fmaxf(m, fmaxf(fabsf(v[u].x), fabsf(v[u].y)));
-    }
-    m = block_max256(m, red);
-    const int e = split_exponent(m);
-    if (threadIdx.x == 0) col_exp[a_idx] = e;
-    if (k0 < Kp) split_store4(v, e, r_hi, A * Kp, k0);  // Kp is a multiple of 8
-    return;
-  }
-  for (int64_t q = threadIdx.x; q < Kp; q += blockDim.x) {
-    const float2 c = value(q);
-    m = fmaxf(m, fmaxf(fabsf(c.x), fabsf(c.y)));
-  }
-  m = block_max256(m, red);
-  const int e = split_exponent(m);
-  if (threadIdx.x == 0) col_exp[a_idx] = e;
   for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < Kp; k0 += 4 * (int64_t)blockDim.x) {
     float2 v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = value(k0 + u);
-    split_store4(v, e, r_hi, A * Kp, k0);
+    for (int u = 0; u < 4; ++u) {
+      const int64_t q = k0 + u;
+      float2 c = make_float2(0.f, 0.f), cd;
+      if (q == 2 * L_max + 1)
+        block_coef(a, sa, ca, 0, true, c, cd);
+      else if (q <= 2 * L_max && q >= L_max - L && q <= L_max + L)
+        block_coef(a, sa, ca, (int)(q - L_max), false, c, cd);
+      v[u] = c;
+    }
+    split_store4(v, FG_COEF_EXP, r_hi, A * Kp, k0);  // Kp is a multiple of 8
   }
 }
 
@@ -204,15 +200,18 @@ __global__ void grad_final_kernel(const double* __restrict__ partial, int nchunk
 // imaginary part.
 // G > 0: each thread keeps its G groups of 4 consecutive entries in registers between
 // the max and the split (one read of the column; needs Np <= 1024 G).  G == 0: any Np,
-// the column is read twice.
-template <int G>
-__global__ void __launch_bounds__(256) split_signals_kernel(const float2* __restrict__ X, int64_t B, int64_t N,
+// the column is read twice.  XR: the signals are real float32 (B x N), the imaginary
+// parts zero.
+template <int G, bool XR>
+__global__ void __launch_bounds__(256) split_signals_kernel(const void* __restrict__ Xv, int64_t B, int64_t N,
                                                             int64_t Np, int64_t rows_pad, __half* __restrict__ planes,
                                                             int* __restrict__ col_exp, int* __restrict__ bimag) {
   const int64_t j = blockIdx.x;
   const int64_t plane = rows_pad * Np;
   __half* r_hi = planes + j * Np;
-  const float2* x = X + j * N;
+  const float2* x = static_cast<const float2*>(Xv) + j * N;
+  const float* xr = static_cast<const float*>(Xv) + j * N;
+  auto load = [&](int64_t k) -> float2 { return XR ? make_float2(xr[k], 0.f) : x[k]; };
   if (j >= B) {  // padding rows are zero
     for (int64_t k = threadIdx.x; k < Np; k += blockDim.x) {
       r_hi[k] = r_hi[plane + k] = r_hi[2 * plane + k] = r_hi[3 * plane + k] = __float2half(0.f);
@@ -229,7 +228,7 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const float2* __rest
       const int64_t k0 = 4 * ((int64_t)threadIdx.x + (int64_t)g * blockDim.x);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        v[g][u] = k0 + u < N ? x[k0 + u] : make_float2(0.f, 0.f);
+        v[g][u] = k0 + u < N ? load(k0 + u) : make_float2(0.f, 0.f);
         m = fmaxf(m, fmaxf(fabsf(v[g][u].x), fabsf(v[g][u].y)));
         im |= !(v[g][u].y == 0.f);
       }
@@ -248,7 +247,7 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const float2* __rest
     }
   } else {
     for (int64_t k = threadIdx.x; k < N; k += blockDim.x) {
-      const float2 v = x[k];
+      const float2 v = load(k);
       m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
       im |= !(v.y == 0.f);
     }
@@ -262,7 +261,7 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const float2* __rest
     for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < Np; k0 += 4 * (int64_t)blockDim.x) {
       float2 v[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = k0 + u < N ? x[k0 + u] : make_float2(0.f, 0.f);
+      for (int u = 0; u < 4; ++u) v[u] = k0 + u < N ? load(k0 + u) : make_float2(0.f, 0.f);
       split_store4(v, e, r_hi, plane, k0);
     }
   }
@@ -273,10 +272,10 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const float2* __rest
 cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* coef, float2* coefd, int64_t ldb,
                       int64_t ldj, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  dim3 grid((B + 127) / 128, 2 * L + 2);
+  dim3 grid((B + 31) / 32, (2 * L + 2 + 7) / 8);
   FgTimed timed(FGFRFT_KC_COEFFS, s);
   fg_note_launch(FGFRFT_KC_COEFFS);
-  coeffs_kernel<<<grid, 128, 0, s>>>(alpha, B, L, adjoint ? -1.0 : 1.0, coef, coefd, ldb, ldj, 0, 2 * L + 1);
+  coeffs_kernel<<<grid, 256, 0, s>>>(alpha, B, L, adjoint ? -1.0 : 1.0, coef, coefd, ldb, ldj, 0, 2 * L + 1);
   return cudaGetLastError();
 }
 
@@ -297,8 +296,8 @@ cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N
   return cudaGetLastError();
 }
 
-cudaError_t fg_split_signals(const float2* X, int64_t B, int64_t N, int64_t Np, int64_t rows_pad, __half* planes,
-                             int* col_exp, cudaStream_t s, int* bimag) {
+cudaError_t fg_split_signals(const void* X, int64_t B, int64_t N, int64_t Np, int64_t rows_pad, __half* planes,
+                             int* col_exp, cudaStream_t s, int* bimag, bool x_real) {
   if (rows_pad <= 0) return cudaSuccess;
   if (bimag) {
     const cudaError_t e = cudaMemsetAsync(bimag, 0, sizeof(int), s);
@@ -307,14 +306,18 @@ cudaError_t fg_split_signals(const float2* X, int64_t B, int64_t N, int64_t Np, 
   FgTimed timed(FGFRFT_KC_SPLIT_SIGNALS, s);
   fg_note_launch(FGFRFT_KC_SPLIT_SIGNALS);
   const unsigned grid = (unsigned)rows_pad;
-  if (Np <= 1024)
-    split_signals_kernel<1><<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
-  else if (Np <= 2048)
-    split_signals_kernel<2><<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
-  else if (Np <= 4096)
-    split_signals_kernel<4><<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
-  else
-    split_signals_kernel<0><<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
+  auto go = [&](auto kern) { kern<<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag); };
+  if (x_real) {
+    if (Np <= 1024) go(split_signals_kernel<1, true>);
+    else if (Np <= 2048) go(split_signals_kernel<2, true>);
+    else if (Np <= 4096) go(split_signals_kernel<4, true>);
+    else go(split_signals_kernel<0, true>);
+  } else {
+    if (Np <= 1024) go(split_signals_kernel<1, false>);
+    else if (Np <= 2048) go(split_signals_kernel<2, false>);
+    else if (Np <= 4096) go(split_signals_kernel<4, false>);
+    else go(split_signals_kernel<0, false>);
+  }
   return cudaGetLastError();
 }
 

@@ -1,5 +1,7 @@
 // Tensor-core (tcgen05) GEMM paths: split-fp16 operands, FP32 accumulators in TMEM.
 #pragma once
+#include <vector>
+
 #include "internal.h"
 
 // True when the tcgen05 kernels are compiled in and the current device is sm_103.
@@ -17,8 +19,8 @@ struct TcGroupedArgs {
   int64_t groups;
   const int64_t* gstart;   // host: first column of each group
   const int64_t* gcount;   // host: columns of each group
-  const float2* X;         // B x N signals
-  float2* Y;               // B x N outputs
+  const void* X;           // B x N c64 signals (real float32 with x_real)
+  float2* Y;               // B x N c64 outputs (real float32 with y_real)
   __half* Xs;              // work: [4][xs_rows][Np] split signals
   int64_t xs_rows;
   int* col_exp;            // work: [xs_rows]
@@ -28,8 +30,16 @@ struct TcGroupedArgs {
   uint32_t* status;
   bool real_a;             // every Q_g is real (imaginary planes zero): 6 MMAs per k16 step
   int* bimag;              // work: one word, 0 after the split when every signal is real
+  const int4* tiles_dev;   // optional: the tile table (fg_tc_grouped_tiles) already on the device
+  int64_t ntiles;
+  bool x_split_done;       // Xs, col_exp and bimag already hold this X (a second GEMM on it)
+  bool x_real;             // X is real float32
+  bool y_real;             // write only the real parts (the caller knows the products are real)
 };
 cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s);
+// Tile table of the grouped GEMM: {row tile, plane base of Q_g, first column, end column}.
+void fg_tc_grouped_tiles(int64_t N, int64_t groups, const int64_t* gstart, const int64_t* gcount,
+                         std::vector<int4>& tiles);
 
 // Y[:, j] = sum_b coef[b][j] A_b X[:, j] over the stored blocks (stacked path),
 // D likewise with coefd (dual accumulator, may be NULL).
@@ -37,7 +47,7 @@ struct TcStackedArgs {
   int64_t N, Np, plane_elems;
   const __half* stack;     // [nblk_total][4][plane_elems]
   int b0, nb_pow, p_blk;
-  const float2* X;
+  const void* X;           // B x N c64 signals (real float32 with x_real)
   float2* Y;
   float2* D;
   const float2* coef;      // [nb_pow + 1][B]
@@ -51,6 +61,7 @@ struct TcStackedArgs {
   uint32_t* status;
   bool real_a;             // every stored block is real (real F)
   int* bimag;              // work: one word, 0 after the split when every signal is real
+  bool x_real;             // X is real float32
 };
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s);
 

@@ -20,8 +20,9 @@ from .build import LIB
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_NOT_UNITARY, ERR_AMBIGUOUS_SPECTRUM = 1, 2, 3, 4
 ERR_NO_MEMORY, ERR_CUDA, ERR_TIMEOUT = 5, 6, 7
-STORE_C64, STORE_SPLIT_F16, STORE_ENTRY_F16 = 1, 2, 4
+STORE_C64, STORE_SPLIT_F16, STORE_ENTRY_F16, STORE_HALF_F16 = 1, 2, 4, 8
 ADJOINT, SHARED_ALPHA = 1, 2
+REAL_SIGNALS, REAL_OUTPUT = 0x100, 0x200
 PATH_PLAIN, PATH_ASSEMBLED, PATH_STACKED, PATH_STACKED_FP32 = 0x10, 0x20, 0x40, 0x80
 OP_ASSEMBLE, OP_APPLY, OP_GRAD = 1, 2, 3
 
@@ -238,18 +239,24 @@ class Plan:
         return out
 
     def apply(self, alpha, X: torch.Tensor, L: int | None = None, adjoint: bool = False, path: str = "auto",
-              out: torch.Tensor | None = None, stream=None):
+              out: torch.Tensor | None = None, stream=None, real_io: bool = False, real_output: bool = False):
         """Y[j] = Q_L^{alpha_j} X[j] (Def. 2), X of shape (B, N), one signal per row.
 
-        A CPU ``X`` is copied to the device and the result copied back (end to end)."""
+        A CPU ``X`` is copied to the device and the result copied back (end to end).
+        ``real_io``: X is passed as real float32 signals (half the bytes of complex64; the
+        tensor-core paths read it directly); ``real_output`` (with ``real_io``): Y is
+        real float32, for a real F without a -1 eigenvalue (Q is then real)."""
         L = self.L_max if L is None else int(L)
         host = X.device.type == "cpu"
-        Xd = X.to(self.device, dtype=torch.complex64, non_blocking=True).contiguous() if host or \
-            X.dtype != torch.complex64 else X.contiguous()
+        xdt = torch.float32 if real_io else torch.complex64
+        Xd = X.to(self.device, dtype=xdt, non_blocking=True).contiguous() if host or X.dtype != xdt \
+            else X.contiguous()
         B = Xd.shape[0]
         a = _alpha_array(alpha, B)
-        flags = PATHS[path] | (ADJOINT if adjoint else 0)
-        Y = torch.empty_like(Xd) if (out is None or host) else out
+        flags = PATHS[path] | (ADJOINT if adjoint else 0) | (REAL_SIGNALS if real_io else 0) | \
+            (REAL_OUTPUT if real_io and real_output else 0)
+        ydt = torch.float32 if (real_io and real_output) else torch.complex64
+        Y = torch.empty(Xd.shape, dtype=ydt, device=self.device) if (out is None or host) else out
         w = self.work_tensor(OP_APPLY, a, B, L, flags)
         rc = _lib().fgfrft_apply(self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, _ptr(Xd), _ptr(Y), flags,
                                  _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream)))
@@ -297,14 +304,19 @@ class Pipeline:
     """Streams host batches through ``Plan.apply``: the copy of batch k+1 to the device,
     the transform of batch k and the copy of batch k-1 back to the host run on three
     CUDA streams at once, with two device buffers per side.  ``submit`` returns at once;
-    ``wait`` blocks until every submitted batch is back in its host buffer."""
+    ``wait`` blocks until every submitted batch is back in its host buffer.  ``real_io`` /
+    ``real_output`` as in ``Plan.apply`` (real float32 host buffers)."""
 
-    def __init__(self, plan: Plan, shape, L: int | None = None, path: str = "auto"):
+    def __init__(self, plan: Plan, shape, L: int | None = None, path: str = "auto", real_io: bool = False,
+                 real_output: bool = False):
         self.plan, self.L, self.path = plan, plan.L_max if L is None else int(L), path
+        self.real_io, self.real_output = real_io, real_io and real_output
         dev = plan.device
         self.s_in, self.s_run, self.s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-        self.X = [torch.empty(shape, dtype=torch.complex64, device=dev) for _ in range(2)]
-        self.Y = [torch.empty(shape, dtype=torch.complex64, device=dev) for _ in range(2)]
+        xdt = torch.float32 if real_io else torch.complex64
+        ydt = torch.float32 if self.real_output else torch.complex64
+        self.X = [torch.empty(shape, dtype=xdt, device=dev) for _ in range(2)]
+        self.Y = [torch.empty(shape, dtype=ydt, device=dev) for _ in range(2)]
         self.ev_in = [torch.cuda.Event() for _ in range(2)]
         self.ev_run = [torch.cuda.Event() for _ in range(2)]
         self.ev_out = [torch.cuda.Event() for _ in range(2)]
@@ -321,7 +333,8 @@ class Pipeline:
             self.ev_in[b].record(self.s_in)
         self.s_run.wait_event(self.ev_in[b])
         with torch.cuda.stream(self.s_run):
-            self.plan.apply(alpha, self.X[b], self.L, path=self.path, out=self.Y[b], stream=self.s_run)
+            self.plan.apply(alpha, self.X[b], self.L, path=self.path, out=self.Y[b], stream=self.s_run,
+                            real_io=self.real_io, real_output=self.real_output)
             self.ev_run[b].record(self.s_run)
         self.s_out.wait_event(self.ev_run[b])
         with torch.cuda.stream(self.s_out):
