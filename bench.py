@@ -568,7 +568,7 @@ def run_precision(args):
                               "frac_of_hbm": byts / (k1 / max(t1, 1) * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
     # the same order from the half stack (M_0..M_L and P only; M_{-l} read as transposed tiles)
     Qf = plan.assemble([0.37], L)
-    half = FG.Plan(wl.F, L, storage=FG.STORE_HALF_F16)
+    half = FG.Plan(wl.F, L, storage=FG.STORE_HALF)
     FG.timing_reset()
     FG.timing_enable(True)
     _device_time(lambda: half.assemble([0.37], L), 5, 2)

@@ -78,14 +78,16 @@ enum fgfrft_storage {
                                  contiguous (row pitch rounded up to 8); lets the fused
                                  multi-order assembly run as one tensor-core GEMM.
                                  Requires FGFRFT_STORE_SPLIT_F16. */
-  FGFRFT_STORE_HALF_F16 = 8,  /* the split fp16 planes of M_0 .. M_{L_max} and P only
-                                 (L_max + 2 blocks, half the split stack): a negative
+  FGFRFT_STORE_HALF = 8,      /* M_0 .. M_{L_max} and P only (L_max + 2 blocks): a negative
                                  power is read as the conjugate transpose of the stored
                                  positive one, M_{-l} = M_l^H (Prop. 2, as Algorithm 1
-                                 forms it).  Read by the single-order assembly (pairs of
-                                 transposed 64 x 64 tiles, half the bytes), and so by
-                                 fgfrft_assemble and the plain and assembled paths of
-                                 fgfrft_apply; the stacked paths and fgfrft_grad need
+                                 forms it).  Each block is two FP32 planes (re, im) of
+                                 64 x 64 tiles, tiles in row-major order, element (r, c)
+                                 of a tile at r * 64 + (c XOR (r mod 32)); 8 B per entry.
+                                 Read by the single-order assembly (pairs of transposed
+                                 tiles, half the bytes of a full stack), and so by
+                                 fgfrft_assemble, the plain and assembled paths of
+                                 fgfrft_apply and fgfrft_grad; the stacked paths need
                                  FGFRFT_STORE_SPLIT_F16 or FGFRFT_STORE_C64. */
 };
 
@@ -119,7 +121,7 @@ int fgfrft_version(void);
 /* Bytes of device memory a plan for (N, L_max, storage) occupies: the status
  * word, 2 L_max + 2 blocks of N x N entries (M_{-L_max} .. M_{L_max}, then P)
  * in every full storage requested (L_max + 2 blocks M_0 .. M_{L_max}, P for
- * FGFRFT_STORE_HALF_F16), each storage padded to 256 B.  Returns 0 for invalid
+ * FGFRFT_STORE_HALF), each storage padded to 256 B.  Returns 0 for invalid
  * arguments (N < 1, L_max < 0, no storage of the blocks, an unknown bit, or
  * FGFRFT_STORE_ENTRY_F16 without FGFRFT_STORE_SPLIT_F16). */
 size_t fgfrft_plan_bytes(int64_t N, int L_max, int storage);
@@ -167,9 +169,10 @@ int fgfrft_plan_info(fgfrft_plan p, int64_t* N, int* L_max, int* storage, int* r
 
 /* Device pointer to stored block l (-L_max <= l <= L_max, or l = L_max + 1 for
  * P) in the given storage (one bit), and the element stride between blocks.
- * For FGFRFT_STORE_C64 the block is N x N c64; for FGFRFT_STORE_SPLIT_F16 and
- * FGFRFT_STORE_HALF_F16 it is four consecutive fp16 planes of N rows of pitch
- * round_up(N, 8).  NULL if absent (a negative l in FGFRFT_STORE_HALF_F16). */
+ * For FGFRFT_STORE_C64 the block is N x N c64; for FGFRFT_STORE_SPLIT_F16 it is
+ * four consecutive fp16 planes of N rows of pitch round_up(N, 8); for
+ * FGFRFT_STORE_HALF the two tiled FP32 planes described there.  NULL if absent
+ * (a negative l in FGFRFT_STORE_HALF). */
 const void* fgfrft_plan_block(fgfrft_plan p, int storage, int l, int64_t* block_stride_elems);
 
 /* Synchronise the stream, read the plan's device status word and clear it:
@@ -196,7 +199,7 @@ size_t fgfrft_work_bytes(fgfrft_plan p, int op, const double* alpha_host, int64_
  *   alpha_host  A orders.
  *   Q_dev       A x N x N c64 output, Q_dev[a][i][k] = (Q_L^{alpha_a})_{ik}.
  * A = 1 streams the stored blocks once: the L + 2 half-stack blocks as pairs
- * of transposed tiles with FGFRFT_STORE_HALF_F16, else the 2L + 2 c64 blocks
+ * of transposed tiles with FGFRFT_STORE_HALF, else the 2L + 2 c64 blocks
  * (the two real split planes for a real F) with bulk-copy staging.  A > 1
  * without an entry-major copy repeats that per order.  A > 1 reads each stored entry once for all A
  * outputs: as one tensor-core GEMM over the entry-major split stack when the plan

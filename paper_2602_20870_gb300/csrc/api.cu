@@ -18,7 +18,8 @@ inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 struct Layout {
-  int64_t blk_elems, Np, plane_elems, Kp, planeT;
+  int64_t blk_elems, Np, plane_elems, Kp, planeT, hplane;
+  int nt;
   size_t off_c64, off_f16, off_f16T, off_h16, total;
 };
 
@@ -37,9 +38,10 @@ Layout plan_layout(int64_t N, int L_max, int storage) {
   l.planeT = round_up(N * N * l.Kp, 128);
   l.off_f16T = off;
   if (storage & FGFRFT_STORE_ENTRY_F16) off = align_up(off + (size_t)4 * l.planeT * sizeof(__half));
+  l.nt = (int)((N + 63) / 64);
+  l.hplane = (int64_t)l.nt * l.nt * 4096;
   l.off_h16 = off;
-  if (storage & FGFRFT_STORE_HALF_F16)
-    off = align_up(off + (size_t)(L_max + 2) * 4 * l.plane_elems * sizeof(__half));
+  if (storage & FGFRFT_STORE_HALF) off = align_up(off + (size_t)(L_max + 2) * 2 * l.hplane * sizeof(float));
   l.total = off;
   return l;
 }
@@ -117,7 +119,7 @@ int grad_path(const fgfrft_plan_s* p, const std::vector<double>& a, int flags) {
   int path = flags & FGFRFT_PATH_MASK;
   if (path) return path;
   const bool tc = fg_tc_available();
-  const bool single = p->h16 || p->c64 || (p->real && p->f16);  // single-order kernels available
+  const bool single = p->h32 || p->c64 || (p->real && p->f16);  // single-order kernels available
   if (!p->f16 && !p->c64) return tc ? FGFRFT_PATH_ASSEMBLED : FGFRFT_PATH_PLAIN;
   int64_t min_run = INT64_MAX;
   for (auto& r : order_runs(a)) min_run = std::min(min_run, r.second);
@@ -188,11 +190,11 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
     ta.re_only = p->real && p->r_neg1 == 0;  // real blocks, P = 0: every Q_a is real
     return fg_tc_assemble(ta, s);
   }
-  if (p->h16) {  // half stack: per order, pairs of transposed tiles (half the bytes)
+  if (p->h32) {  // half stack: per order, pairs of transposed tiles (half the bytes)
     cudaError_t e = fg_coeffs(alpha_dev, (int)A, L, false, w.coef, nullptr, 1, 2 * L + 2, s);
     if (e != cudaSuccess) return e;
     for (int64_t a = 0; a < A; ++a) {
-      e = fg_assemble_half(p->h16, p->plane_elems, p->L_max, L, !p->real, p->r_neg1 > 0, p->N, p->Np,
+      e = fg_assemble_half(p->h32, p->hplane, p->nt, p->L_max, L, !p->real, p->r_neg1 > 0, p->N, p->Np,
                            w.coef + a * (2 * L + 2), Qc ? Qc + a * p->N * p->N : nullptr,
                            Qs ? Qs + a * 4 * p->plane_elems : nullptr, p->plane_elems,
                            !(p->real && p->r_neg1 == 0), p->dstatus, s);
@@ -215,8 +217,8 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
 // One order on the single-order kernels: coef = [2L+2] (powers at L + l, P at 2L + 1).
 cudaError_t assemble_one(const fgfrft_plan_s* p, const float2* coef, int L, float2* Qc, __half* Qs, cudaStream_t s) {
   const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
-  if (p->h16)
-    return fg_assemble_half(p->h16, p->plane_elems, p->L_max, L, !p->real, p->r_neg1 > 0, p->N, p->Np, coef, Qc, Qs,
+  if (p->h32)
+    return fg_assemble_half(p->h32, p->hplane, p->nt, p->L_max, L, !p->real, p->r_neg1 > 0, p->N, p->Np, coef, Qc, Qs,
                             p->plane_elems, !(p->real && p->r_neg1 == 0), p->dstatus, s);
   if (p->real && p->f16)
     return fg_assemble_single_real(p->f16, 4 * p->plane_elems, p->plane_elems, b0, nb, pb, p->N, p->Np, coef, Qc, Qs,
@@ -343,8 +345,8 @@ int fgfrft_version(void) { return 100; }
 
 size_t fgfrft_plan_bytes(int64_t N, int L_max, int storage) {
   if (N < 1 || N > 65536 || L_max < 0 || L_max > 1000) return 0;
-  const int known = FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16 | FGFRFT_STORE_ENTRY_F16 | FGFRFT_STORE_HALF_F16;
-  if ((storage & (FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16 | FGFRFT_STORE_HALF_F16)) == 0) return 0;
+  const int known = FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16 | FGFRFT_STORE_ENTRY_F16 | FGFRFT_STORE_HALF;
+  if ((storage & (FGFRFT_STORE_C64 | FGFRFT_STORE_SPLIT_F16 | FGFRFT_STORE_HALF)) == 0) return 0;
   if (storage & ~known) return 0;
   if ((storage & FGFRFT_STORE_ENTRY_F16) && !(storage & FGFRFT_STORE_SPLIT_F16)) return 0;
   return plan_layout(N, L_max, storage).total;
@@ -383,7 +385,9 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   p->c64 = (storage & FGFRFT_STORE_C64) ? (float2*)(pm + lay.off_c64) : nullptr;
   p->f16 = (storage & FGFRFT_STORE_SPLIT_F16) ? (__half*)(pm + lay.off_f16) : nullptr;
   p->f16T = (storage & FGFRFT_STORE_ENTRY_F16) ? (__half*)(pm + lay.off_f16T) : nullptr;
-  p->h16 = (storage & FGFRFT_STORE_HALF_F16) ? (__half*)(pm + lay.off_h16) : nullptr;
+  p->h32 = (storage & FGFRFT_STORE_HALF) ? (float*)(pm + lay.off_h16) : nullptr;
+  p->nt = lay.nt;
+  p->hplane = lay.hplane;
   p->Kp = lay.Kp;
   p->planeT = lay.planeT;
 
@@ -480,9 +484,8 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   };
   // half stack: M_0 .. M_L_max at blocks 0 .. L_max, P at L_max + 1
   auto store_half = [&](int hb, const double2* M) -> bool {
-    if (!p->h16) return true;
-    return fg_store_block(N, M, false, nullptr, p->h16 + (int64_t)hb * 4 * p->plane_elems, p->Np, p->plane_elems,
-                          s) == cudaSuccess;
+    if (!p->h32) return true;
+    return fg_store_half(N, M, p->h32 + (int64_t)hb * 2 * p->hplane, p->nt, p->hplane, s) == cudaSuccess;
   };
   if (!store(blk_of_P(p), Cm, false) || !store_half(L_max + 1, Cm)) return fail(FGFRFT_ERR_CUDA);
   if (fg_zaxpby_identity(N, make_double2(-1.0, 0.0), Cm, zero, one, Am, s)) return fail(FGFRFT_ERR_CUDA);
@@ -527,9 +530,9 @@ const void* fgfrft_plan_block(fgfrft_plan p, int storage, int l, int64_t* block_
     if (block_stride_elems) *block_stride_elems = 4 * p->plane_elems;
     return p->f16 + (int64_t)blk * 4 * p->plane_elems;
   }
-  if (storage == FGFRFT_STORE_HALF_F16 && p->h16 && l >= 0) {
-    if (block_stride_elems) *block_stride_elems = 4 * p->plane_elems;
-    return p->h16 + (int64_t)l * 4 * p->plane_elems;  // l = L_max + 1 is P
+  if (storage == FGFRFT_STORE_HALF && p->h32 && l >= 0) {
+    if (block_stride_elems) *block_stride_elems = 2 * p->hplane;
+    return p->h32 + (int64_t)l * 2 * p->hplane;  // l = L_max + 1 is P
   }
   return nullptr;
 }
@@ -591,7 +594,7 @@ int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, v
     return FGFRFT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   AssembleWork w = carve_assemble(p, (char*)work, A, L);
-  if (!w.tensor && !p->c64 && !p->h16) return FGFRFT_ERR_UNSUPPORTED;
+  if (!w.tensor && !p->c64 && !p->h32) return FGFRFT_ERR_UNSUPPORTED;
   CK(fg_h2d(w.alpha_dev, a.data(), (size_t)A * sizeof(double), s));
   CK(run_assemble(p, w, w.alpha_dev, A, L, (float2*)Q_dev, nullptr, s));
   return FGFRFT_OK;
@@ -613,7 +616,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
   float2* Y = (float2*)Y_dev;
   switch (path) {
     case FGFRFT_PATH_PLAIN: {
-      if (!p->c64 && !(p->real && p->f16) && !p->h16) return FGFRFT_ERR_UNSUPPORTED;
+      if (!p->c64 && !(p->real && p->f16) && !p->h32) return FGFRFT_ERR_UNSUPPORTED;
       if (groups > 65535) return FGFRFT_ERR_UNSUPPORTED;
       std::vector<double> ga((size_t)groups);
       for (int64_t g = 0; g < groups; ++g) ga[(size_t)g] = a[(size_t)runs[(size_t)g].first];
@@ -682,7 +685,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
     }
     case FGFRFT_PATH_ASSEMBLED: {
       if (!fg_tc_available()) return FGFRFT_ERR_UNSUPPORTED;
-      if (D_dev ? !(p->h16 || p->c64 || (p->real && p->f16)) : !(p->h16 || (p->f16 && (p->c64 || p->f16T))))
+      if (D_dev ? !(p->h32 || p->c64 || (p->real && p->f16)) : !(p->h32 || (p->f16 && (p->c64 || p->f16T))))
         return FGFRFT_ERR_UNSUPPORTED;
       std::vector<double> ga((size_t)groups);
       std::vector<int64_t> gstart((size_t)groups), gcount((size_t)groups);
@@ -693,7 +696,8 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       }
       // every host table of the call goes up first, so no copy waits in the middle of the call
       std::vector<int4> tiles;
-      fg_tc_grouped_tiles(p->N, groups, gstart.data(), gcount.data(), tiles);
+      fg_tc_grouped_tiles(p->N, groups, gstart.data(), gcount.data(),
+                          fg_tc_grouped_bn(p->real && p->r_neg1 == 0), tiles);
       if (tiles.size() * sizeof(int4) > w.tc_scratch_bytes) return FGFRFT_ERR_INVALID_ARG;
       CK(fg_h2d(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), s));
       CK(fg_h2d(w.tc_scratch, tiles.data(), tiles.size() * sizeof(int4), s));
@@ -782,7 +786,7 @@ int fgfrft_apply(fgfrft_plan p, const double* alpha_host, int64_t B, int L, cons
   if (flags & FGFRFT_ADJOINT)
     for (auto& v : a) v = -v;
   const int path = choose_path(p, a, flags);
-  if (path == FGFRFT_PATH_PLAIN && !p->c64 && !(p->real && p->f16) && !p->h16) return FGFRFT_ERR_UNSUPPORTED;
+  if (path == FGFRFT_PATH_PLAIN && !p->c64 && !(p->real && p->f16) && !p->h32) return FGFRFT_ERR_UNSUPPORTED;
   return apply_impl(p, a, B, L, X_dev, Y_dev, nullptr, path, work, work_bytes, (cudaStream_t)stream, real_io);
 }
 

@@ -473,48 +473,32 @@ cudaError_t launch_multi(const float2* stack, int64_t blk_elems, int b0, int nb_
 // (I, K), (K, I), I <= K, reading both tiles of every stored block once:
 //   Q[I,K] += c_l M_l[I,K] + c_{-l} (M_l[K,I])^H,   Q[K,I] += c_l M_l[K,I] + c_{-l} (M_l[I,K])^H,
 // so each stored entry serves one positive and one negative power and the stack streams
-// half the bytes of a full one.  Tiles arrive by TMA with the 128-byte swizzle; warp w owns
-// rows 8w..8w+7 of a tile and reads them with ldmatrix, the transposed operand with
-// ldmatrix.trans (both free of bank conflicts on the swizzled layout).  Thread t of a warp
-// holds columns 2(t%4), 2(t%4)+1 of row t/4 of each 8 x 8 sub-block.  P (stored once)
-// comes last with its complex coefficient.
+// half the bytes of a full one.  The stack holds FP32 tiles of 16 KB per plane, each row r
+// permuted by c -> c ^ (r & 31): one bulk copy brings a tile into shared memory, and a
+// warp reading one row (lanes = columns) or one column (lanes = rows) of it touches 32
+// different banks.  Warp w owns rows 8w..8w+7 of a tile; lane t its columns t and t + 32.
+// A producer warp keeps the ring full; consumer warps release each stage on an mbarrier.
+// P (stored once) comes last with its complex coefficient.
 // ---------------------------------------------------------------------------
 constexpr int KH_T = 64;
-constexpr int KH_THREADS = 256;
-constexpr int KH_TILE = KH_T * KH_T * 2;  // bytes of one fp16 plane of one tile
+constexpr int KH_WARPS = 8;                      // consumer warps
+constexpr int KH_THREADS = 32 * (KH_WARPS + 1);  // + one producer warp
+constexpr int KH_TILE = KH_T * KH_T * 4;         // bytes of one FP32 plane of one tile
 
 template <bool CPLX>
 struct KHCfg {
-  static constexpr int PLANES = CPLX ? 4 : 2;
+  static constexpr int PLANES = CPLX ? 2 : 1;        // re (, im)
   static constexpr int STAGE = 2 * PLANES * KH_TILE;  // both tiles of a pair
   static constexpr int STAGES = CPLX ? 3 : 6;
 };
 
 struct KHCtl {
-  uint64_t full[8];
+  uint64_t full[8];   // stage loaded (bulk-copy bytes)
+  uint64_t empty[8];  // stage consumed (one arrival per consumer warp)
   float cpos[K1_MAXBLK];  // c_l, l = 0..L
   float cneg[K1_MAXBLK];  // c_{-l} (0 for l = 0)
   float2 cp;              // e^{j pi a}
 };
-
-// byte address of (row, col) in a swizzled 64 x 64 fp16 tile; col a multiple of 8
-__device__ __forceinline__ uint32_t kh_addr(uint32_t tile, int row, int col) {
-  return tile + (uint32_t)row * 128u + ((uint32_t)(((col >> 3) ^ row) & 7) << 4);
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t (&r)[4]) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(addr));
-}
-
-__device__ __forceinline__ float2 h2f(uint32_t v) { return __half22float2(*reinterpret_cast<const __half2*>(&v)); }
 
 // (I, K) of pair p: row I of the upper triangle holds nt - I pairs, K = I .. nt-1.  A
 // single-precision estimate of the row (FP64 is a slow pipe here), corrected exactly.
@@ -530,33 +514,11 @@ __device__ __forceinline__ void kh_pair(int64_t p, int nt, int& I, int& K) {
   K = (int)(i + (p - start(i)));
 }
 
-// The fragment sum hi + lo of an 8 x 8 sub-block pair (row-block rb, column-block cb) of
-// the planes at `tile` (plane stride KH_TILE); trans reads the transposed sub-block.
-template <bool TRANS>
-__device__ __forceinline__ void kh_frag(uint32_t tile, int rb, int cb4, int lane, float2 (&v)[4]) {
-  uint32_t hi[4], lo[4];
-  // x4: matrices m = 0..3 are column blocks cb4 + m (non-trans) or row blocks cb4 + m (trans)
-  const int r = TRANS ? 8 * (cb4 + (lane >> 3)) + (lane & 7) : 8 * rb + (lane & 7);
-  const int c = TRANS ? 8 * rb : 8 * (cb4 + (lane >> 3));
-  if (TRANS) {
-    ldsm_x4_t(kh_addr(tile, r, c), hi);
-    ldsm_x4_t(kh_addr(tile + KH_TILE, r, c), lo);
-  } else {
-    ldsm_x4(kh_addr(tile, r, c), hi);
-    ldsm_x4(kh_addr(tile + KH_TILE, r, c), lo);
-  }
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const float2 a = h2f(hi[m]), b = h2f(lo[m]);
-    v[m] = make_float2(a.x + b.x, a.y + b.y);
-  }
-}
-
 template <bool CPLX, bool SPLIT>
 __global__ void __launch_bounds__(KH_THREADS, 1) assemble_half_kernel(
-    const __grid_constant__ CUtensorMap tm, int nt, int L, int blk_P, int has_p, const float2* __restrict__ coef,
-    int64_t N, float2* __restrict__ Q, __half* __restrict__ Qs, int64_t Np, int64_t q_plane, int write_im,
-    uint32_t* status) {
+    const float* __restrict__ stack, int64_t hplane, int nt, int L, int blk_P, int has_p,
+    const float2* __restrict__ coef, int64_t N, float2* __restrict__ Q, __half* __restrict__ Qs, int64_t Np,
+    int64_t q_plane, int write_im, uint32_t* status) {
   using Cfg = KHCfg<CPLX>;
   constexpr int PL = Cfg::PLANES;
   extern __shared__ uint8_t smem_raw[];
@@ -569,7 +531,10 @@ __global__ void __launch_bounds__(KH_THREADS, 1) assemble_half_kernel(
   }
   if (tid == 0) {
     sm.cp = has_p ? coef[2 * L + 1] : make_float2(0.f, 0.f);
-    for (int s = 0; s < Cfg::STAGES; ++s) mbar_init(&sm.full[s], 1);
+    for (int s = 0; s < Cfg::STAGES; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], KH_WARPS);
+    }
     fence_barrier_init();
   }
   __syncthreads();
@@ -578,48 +543,82 @@ __global__ void __launch_bounds__(KH_THREADS, 1) assemble_half_kernel(
   const int nbi = L + 1 + (has_p ? 1 : 0);  // items per pair: blocks 0..L, then P
   const int64_t my_pairs = npairs > blockIdx.x ? (npairs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t items = my_pairs * nbi;
-  // producer cursor (thread 0): stage, pair and block of the next copy, issued in order
-  int ps = 0, pj = 0, pI = 0, pK = 0;
-  int64_t ppr = blockIdx.x;
-  if (my_pairs > 0) kh_pair(ppr, nt, pI, pK);
-  auto issue = [&]() {
-    const int s = ps;
-    const int j = pj;
-    const int blk = j <= L ? j : blk_P;
-    const int I = pI, K = pK;
-    const bool diag = I == K;
-    uint8_t* st = base + s * Cfg::STAGE;
-    mbar_arrive_expect_tx(&sm.full[s], (uint32_t)(PL * KH_TILE * (diag ? 1 : 2)));
+
+  if (warp == KH_WARPS) {
+    // ---------------------------------------------------------------- producer warp
+    if (lane == 0) {
+      int ps = 0, pj = 0, pI = 0, pK = 0;
+      int64_t ppr = blockIdx.x;
+      if (my_pairs > 0) kh_pair(ppr, nt, pI, pK);
+      uint32_t issued[Cfg::STAGES] = {};
+      uint32_t eph = 1;  // a fresh barrier's preceding phase counts as complete
+      bool pok = true;
+      uint64_t policy = policy_evict_first();
+      for (int64_t it = 0; pok && it < items; ++it) {
+        const int s = ps;
+        if (!mbar_wait(&sm.empty[s], eph, status)) {
+          pok = false;
+          break;
+        }
+        const int blk = pj <= L ? pj : blk_P;
+        const bool diag = pI == pK;
+        uint8_t* st = base + s * Cfg::STAGE;
+        mbar_arrive_expect_tx(&sm.full[s], (uint32_t)(PL * KH_TILE * (diag ? 1 : 2)));
+        const float* bb = stack + (int64_t)blk * 2 * hplane;
 #pragma unroll
-    for (int q = 0; q < PL; ++q) tma_load_3d(st + q * KH_TILE, &tm, K * KH_T, I * KH_T, 4 * blk + q, &sm.full[s]);
-    if (!diag) {
-#pragma unroll
-      for (int q = 0; q < PL; ++q)
-        tma_load_3d(st + (PL + q) * KH_TILE, &tm, I * KH_T, K * KH_T, 4 * blk + q, &sm.full[s]);
+        for (int q = 0; q < PL; ++q) {
+          bulk_g2s_evict_first(st + q * KH_TILE, bb + q * hplane + ((int64_t)pI * nt + pK) * 4096, KH_TILE,
+                               &sm.full[s], policy);
+          if (!diag)
+            bulk_g2s_evict_first(st + (PL + q) * KH_TILE, bb + q * hplane + ((int64_t)pK * nt + pI) * 4096, KH_TILE,
+                                 &sm.full[s], policy);
+        }
+        issued[s]++;
+        if (++ps == Cfg::STAGES) {
+          ps = 0;
+          eph ^= 1u;
+        }
+        if (++pj == nbi) {
+          pj = 0;
+          ppr += gridDim.x;
+          if (ppr < npairs) kh_pair(ppr, nt, pI, pK);
+        }
+      }
+      if (!pok) {  // wait (bounded) until every issued copy has landed
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+          if (!issued[s]) continue;
+          const uint32_t par = (issued[s] - 1) & 1;
+          const uint64_t t0 = global_timer_ns();
+          while (!mbar_try_wait(&sm.full[s], par) && global_timer_ns() - t0 < FG_WAIT_LIMIT_NS) {
+          }
+        }
+      }
     }
-    if (++ps == Cfg::STAGES) ps = 0;
-    if (++pj == nbi) {
-      pj = 0;
-      ppr += gridDim.x;
-      if (ppr < npairs) kh_pair(ppr, nt, pI, pK);
-    }
-  };
-  if (tid == 0) {
-    const int64_t pre = items < Cfg::STAGES ? items : Cfg::STAGES;
-    for (int64_t it = 0; it < pre; ++it) issue();
+    return;
   }
 
-  // accumulators: [tile (I,K) / (K,I)][column half][sub-block] x 2 consecutive columns
-  float2 re[2][2][4], im[2][2][4];
+  // ------------------------------------------------------------------ consumer warps
+  // accumulators: [tile (I,K) / (K,I)][row of the warp][column half]
+  float re[2][8][2], im[2][8][2];
 #pragma unroll
   for (int o = 0; o < 2; ++o)
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int m = 0; m < 4; ++m) re[o][h][m] = im[o][h][m] = make_float2(0.f, 0.f);
+      for (int h = 0; h < 2; ++h) re[o][r][h] = im[o][r][h] = 0.f;
+  // element offsets in a swizzled tile, the same for every stage: (row 8w + r, column
+  // lane + 32h) read directly, and the transposed element (lane + 32h, 8w + r)
+  int offD[8][2], offT[8][2];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int row = 8 * warp + r, col = lane + 32 * h;
+      offD[r][h] = row * KH_T + (col ^ (row & 31));
+      offT[r][h] = col * KH_T + (row ^ (col & 31));
+    }
 
   bool ok = true;
-  // consumer cursor: stage and parity, block j of pair (I, K)
   int cs_ = 0, cj = 0, I = 0, K = 0;
   uint32_t parity = 0;
   int64_t cpr = blockIdx.x;
@@ -629,115 +628,103 @@ __global__ void __launch_bounds__(KH_THREADS, 1) assemble_half_kernel(
     const int j = cj;
     const bool diag = I == K;
     if (ok) ok = mbar_wait(&sm.full[s], parity, status);
-    const uint32_t tA = smem_u32(base + s * Cfg::STAGE);
-    const uint32_t tB = diag ? tA : tA + PL * KH_TILE;
-    if (ok && j <= L) {
+    if (!ok) break;  // the producer gives up on its own bounded wait
+    const float* tA = reinterpret_cast<const float*>(base + s * Cfg::STAGE);
+    const float* tB = diag ? tA : tA + PL * (KH_TILE / 4);
+    const int no = diag ? 1 : 2;
+    if (j <= L) {
       const float c = sm.cpos[j], cm = sm.cneg[j];
+      for (int o = 0; o < no; ++o) {
+        // o = 0: Q[I,K] from D = M[I,K] and T = M[K,I] read transposed; o = 1: Q[K,I] from B and A
+        const float* tD = o ? tB : tA;
+        const float* tT = o ? tA : tB;
+        float d[8][2], t[8][2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+        for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int o = 0; o < 2; ++o) {
-          if (o == 1 && diag) continue;
-          // o = 0: Q[I,K] from A = M[I,K] and A' = M[K,I]^T; o = 1: Q[K,I] from B and A^T
-          const uint32_t tD = o ? tB : tA, tT = o ? tA : tB;
-          float2 d[4], t[4];
-          kh_frag<false>(tD, warp, 4 * h, lane, d);
-          if (cm != 0.f) kh_frag<true>(tT, warp, 4 * h, lane, t);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            re[o][h][m].x = fmaf(c, d[m].x, re[o][h][m].x);
-            re[o][h][m].y = fmaf(c, d[m].y, re[o][h][m].y);
-            if (cm != 0.f) {
-              re[o][h][m].x = fmaf(cm, t[m].x, re[o][h][m].x);
-              re[o][h][m].y = fmaf(cm, t[m].y, re[o][h][m].y);
-            }
+          for (int h = 0; h < 2; ++h) {
+            d[r][h] = tD[offD[r][h]];
+            t[r][h] = tT[offT[r][h]];  // c_{-l} = 0 only for l = 0: the read is cheaper than a branch
           }
-          if (CPLX) {  // imaginary planes; the transposed term is conjugated
-            kh_frag<false>(tD + 2 * KH_TILE, warp, 4 * h, lane, d);
-            if (cm != 0.f) kh_frag<true>(tT + 2 * KH_TILE, warp, 4 * h, lane, t);
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              im[o][h][m].x = fmaf(c, d[m].x, im[o][h][m].x);
-              im[o][h][m].y = fmaf(c, d[m].y, im[o][h][m].y);
-              if (cm != 0.f) {
-                im[o][h][m].x = fmaf(-cm, t[m].x, im[o][h][m].x);
-                im[o][h][m].y = fmaf(-cm, t[m].y, im[o][h][m].y);
-              }
-            }
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float& a = o ? re[1][r][h] : re[0][r][h];
+            a = fmaf(c, d[r][h], fmaf(cm, t[r][h], a));
           }
+        if (CPLX) {  // imaginary planes; the transposed term is conjugated
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              d[r][h] = tD[KH_TILE / 4 + offD[r][h]];
+              t[r][h] = tT[KH_TILE / 4 + offT[r][h]];
+            }
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              float& a = o ? im[1][r][h] : im[0][r][h];
+              a = fmaf(c, d[r][h], fmaf(-cm, t[r][h], a));
+            }
         }
       }
-    } else if (ok) {  // P with e^{j pi a}: Q[I,K] += cp P[I,K], Q[K,I] += cp P[K,I]
-      const float2 cp = sm.cp;
+    } else {  // P with e^{j pi a} = cr + j ci
+      const float cr = sm.cp.x, ci = sm.cp.y;
+      for (int o = 0; o < no; ++o) {
+        const float* tD = o ? tB : tA;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+        for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int o = 0; o < 2; ++o) {
-          if (o == 1 && diag) continue;
-          const uint32_t tD = o ? tB : tA;
-          float2 pr_[4], pi_[4];
-          kh_frag<false>(tD, warp, 4 * h, lane, pr_);
-          if (CPLX) {
-            kh_frag<false>(tD + 2 * KH_TILE, warp, 4 * h, lane, pi_);
-          } else {
-#pragma unroll
-            for (int m = 0; m < 4; ++m) pi_[m] = make_float2(0.f, 0.f);
+          for (int h = 0; h < 2; ++h) {
+            const float dr = tD[offD[r][h]];
+            const float di = CPLX ? tD[KH_TILE / 4 + offD[r][h]] : 0.f;
+            float& a = o ? re[1][r][h] : re[0][r][h];
+            float& b = o ? im[1][r][h] : im[0][r][h];
+            a += cr * dr - ci * di;
+            b += cr * di + ci * dr;
           }
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            re[o][h][m].x += cp.x * pr_[m].x - cp.y * pi_[m].x;
-            re[o][h][m].y += cp.x * pr_[m].y - cp.y * pi_[m].y;
-            im[o][h][m].x += cp.x * pi_[m].x + cp.y * pr_[m].x;
-            im[o][h][m].y += cp.x * pi_[m].y + cp.y * pr_[m].y;
-          }
-        }
       }
     }
-    __syncthreads();  // every thread is done with slot s
-    if (tid == 0 && ok && it + Cfg::STAGES < items) issue();
+    __syncwarp();  // the warp is done with slot s
+    if (lane == 0) mbar_arrive(&sm.empty[s]);
     if (++cs_ == Cfg::STAGES) {
       cs_ = 0;
       parity ^= 1u;
     }
     if (j == nbi - 1) {
-      // the pair is complete: write Q[I,K] and Q[K,I], scaled by 2^-FG_SPLIT_SHIFT
-      const float inv = 1.0f / (float)(1 << FG_SPLIT_SHIFT);
+      // the pair is complete: write Q[I,K] and Q[K,I]
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
         if (o == 1 && diag) continue;
-        const int R0 = (o ? K : I) * KH_T, C0 = (o ? I : K) * KH_T;
-        const int64_t row = R0 + 8 * warp + (lane >> 2);
+        const int64_t R0 = (int64_t)(o ? K : I) * KH_T, C0 = (int64_t)(o ? I : K) * KH_T;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int r = 0; r < 8; ++r) {
+          const int64_t row = R0 + 8 * warp + r;
 #pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            const int64_t col = C0 + 8 * (4 * h + m) + 2 * (lane & 3);
+          for (int h = 0; h < 2; ++h) {
+            const int64_t col = C0 + lane + 32 * h;
             if (row < N && col < N) {
-              const float2 r2 = make_float2(re[o][h][m].x * inv, re[o][h][m].y * inv);
-              const float2 i2 = make_float2(im[o][h][m].x * inv, im[o][h][m].y * inv);
-              const bool two = col + 1 < N;
               if (!SPLIT) {
-                Q[row * N + col] = make_float2(r2.x, i2.x);
-                if (two) Q[row * N + col + 1] = make_float2(r2.y, i2.y);
+                Q[row * N + col] = make_float2(re[o][r][h], im[o][r][h]);
               } else {
-                // Qs planes (pitch Np, scaled by 2^FG_SPLIT_SHIFT): pairs of columns
+                // Qs planes (pitch Np, scaled by 2^FG_SPLIT_SHIFT)
                 const float sc = (float)(1 << FG_SPLIT_SHIFT);
-                const __half2 rh = __floats2half2_rn(r2.x * sc, r2.y * sc);
-                const float2 rhf = __half22float2(rh);
-                const __half2 rl = __floats2half2_rn(r2.x * sc - rhf.x, r2.y * sc - rhf.y);
-                const __half2 ih = __floats2half2_rn(i2.x * sc, i2.y * sc);
-                const float2 ihf = __half22float2(ih);
-                const __half2 il = __floats2half2_rn(i2.x * sc - ihf.x, i2.y * sc - ihf.y);
-                __half* qq = Qs + row * Np + col;  // col even, Np a multiple of 8: 4-byte aligned
-                *reinterpret_cast<__half2*>(qq) = rh;
-                *reinterpret_cast<__half2*>(qq + q_plane) = rl;
+                const float x = re[o][r][h] * sc, y = im[o][r][h] * sc;
+                const __half2 hi = __floats2half2_rn(x, y);
+                const float2 hf = __half22float2(hi);
+                const __half2 lo = __floats2half2_rn(x - hf.x, y - hf.y);
+                __half* qq = Qs + row * Np + col;
+                qq[0] = __low2half(hi);
+                qq[q_plane] = __low2half(lo);
                 if (write_im) {
-                  *reinterpret_cast<__half2*>(qq + 2 * q_plane) = ih;
-                  *reinterpret_cast<__half2*>(qq + 3 * q_plane) = il;
+                  qq[2 * q_plane] = __high2half(hi);
+                  qq[3 * q_plane] = __high2half(lo);
                 }
               }
             }
-            re[o][h][m] = im[o][h][m] = make_float2(0.f, 0.f);
+            re[o][r][h] = im[o][r][h] = 0.f;
           }
         }
       }
@@ -746,14 +733,6 @@ __global__ void __launch_bounds__(KH_THREADS, 1) assemble_half_kernel(
       if (cpr < npairs) kh_pair(cpr, nt, I, K);
     } else {
       ++cj;
-    }
-  }
-  if (!ok && tid == 0) {
-    for (int s = 0; s < Cfg::STAGES; ++s) {
-      const uint64_t t0 = global_timer_ns();
-      while (!mbar_try_wait(&sm.full[s], 0) && !mbar_try_wait(&sm.full[s], 1)) {
-        if (global_timer_ns() - t0 > FG_WAIT_LIMIT_NS) break;
-      }
     }
   }
 }
@@ -824,14 +803,10 @@ cudaError_t fg_assemble_single_real(const __half* planes, int64_t blk_stride, in
   return cudaGetLastError();
 }
 
-cudaError_t fg_assemble_half(const __half* planes, int64_t plane_elems, int L_max, int L, bool cplx, bool has_p,
+cudaError_t fg_assemble_half(const float* planes, int64_t hplane, int nt, int L_max, int L, bool cplx, bool has_p,
                              int64_t N, int64_t Np, const float2* coef, float2* Q, __half* Qs, int64_t q_plane,
                              bool write_im, uint32_t* status, cudaStream_t s) {
-  if (L + 1 > K1_MAXBLK || L > L_max || N < 1 || N > (int64_t)1 << 24) return cudaErrorInvalidValue;
-  CUtensorMap tm;
-  if (!fg_make_map_f16(&tm, planes, N, N, Np, 4 * (int64_t)(L_max + 2), plane_elems, KH_T, KH_T, 128))
-    return cudaErrorInvalidValue;
-  const int nt = (int)((N + KH_T - 1) / KH_T);
+  if (L + 1 > K1_MAXBLK || L > L_max || N < 1 || nt < 1 || (int64_t)nt * KH_T < N) return cudaErrorInvalidValue;
   const int64_t npairs = (int64_t)nt * (nt + 1) / 2;
   const int blk_P = L_max + 1;
   auto pick = [&](auto kern, size_t smem) -> cudaError_t {
@@ -839,8 +814,8 @@ cudaError_t fg_assemble_half(const __half* planes, int64_t plane_elems, int L_ma
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(npairs, num_sms());
     FgTimed timed(FGFRFT_KC_ASSEMBLE_SINGLE, s);
-    kern<<<(unsigned)grid, KH_THREADS, smem, s>>>(tm, nt, L, blk_P, has_p ? 1 : 0, coef, N, Q, Qs, Np, q_plane,
-                                                  write_im ? 1 : 0, status);
+    kern<<<(unsigned)grid, KH_THREADS, smem, s>>>(planes, hplane, nt, L, blk_P, has_p ? 1 : 0, coef, N, Q, Qs, Np,
+                                                  q_plane, write_im ? 1 : 0, status);
     fg_note_launch(FGFRFT_KC_ASSEMBLE_SINGLE);
     return cudaGetLastError();
   };

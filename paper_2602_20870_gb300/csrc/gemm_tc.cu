@@ -39,7 +39,8 @@ constexpr int TC_PLANE_A = TC_BM * TC_KC * 2;  // 8 KB
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // producer warp, MMA warp, epilogue warps
 constexpr int TC_EPI_WARP0 = 2;
-constexpr int TC_BN_MAX = 128;
+constexpr int TC_BN_MAX = 256;
+constexpr int TC_BN_STD = 128;  // column-tile width of the stacked and complex grouped GEMMs
 
 // Column-tile width BN (complex columns per tile): 128, or 64 for few columns.
 // RB ("resident B"): every tile uses the same B columns (one column tile), so all k-chunks
@@ -51,7 +52,8 @@ template <int BN, bool RB = false, bool RA = false>
 struct TcCfg {
   static constexpr int PLANE_B = BN * TC_KC * 2;
   static constexpr int A_PLANES = RA ? 2 : 4;
-  static constexpr int TMEM_COLS = 4 * BN;  // 2 buffers x [re BN | im BN]
+  // 2 buffers x [re BN | im BN]; BN = 256 has 512 columns: 2 real-only buffers or 1 complex
+  static constexpr int TMEM_COLS = 4 * BN > 512 ? 512 : 4 * BN;
   // kind::f16 instruction descriptor: D f32, A/B f16, both K-major, N = BN, M = 128.
   static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
   static constexpr uint32_t IDESC_NEG_A = IDESC | (1u << 13);
@@ -220,6 +222,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* const stages = bres + res_bytes;
   const int stage_bytes = A_PLANES * TC_PLANE_A + (RB ? 0 : nbp * TC_PLANE_B);
   const int nst = min(TC_MAXST, (p.smem_bytes - (int)sizeof(TcCtl) - res_bytes) / stage_bytes);
+  // TMEM columns of one accumulator buffer, and how many buffers fit (2: the epilogue of one
+  // block overlaps the MMAs of the next)
+  const uint32_t acc_w = (re_only ? 1u : 2u) * (uint32_t)BN;
+  const int nbuf = (uint32_t)Cfg::TMEM_COLS >= 2 * acc_w ? 2 : 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; ++s) {
@@ -318,13 +324,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (RB && blockIdx.x < p.ntiles) ok = tc_wait(&sm.bfull, 0, sm, p.status);
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
         for (int b = 0; ok && b < p.nblk; ++b, ++bc) {
-          const uint32_t buf = bc & 1, tph = (bc >> 1) & 1;
+          const uint32_t buf = nbuf == 2 ? (bc & 1) : 0, tph = nbuf == 2 ? ((bc >> 1) & 1) : (bc & 1);
           if (!tc_wait(&sm.tempty[buf], tph ^ 1, sm, p.status)) {
             ok = false;
             break;
           }
           fence_tc_after();
-          const uint32_t d_re = tmem + buf * (2 * TC_BN);
+          const uint32_t d_re = tmem + buf * acc_w;
           const uint32_t d_im = d_re + TC_BN;
           for (int kc = 0; kc < p.kchunks; ++kc) {
             const int s = s_cur;
@@ -429,13 +435,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
 
       for (int b = 0; b < p.nblk; ++b, ++bc) {
-        const uint32_t buf = bc & 1, tph = (bc >> 1) & 1;
+        const uint32_t buf = nbuf == 2 ? (bc & 1) : 0, tph = nbuf == 2 ? ((bc >> 1) & 1) : (bc & 1);
         if (!tc_wait(&sm.tfull[buf], tph, sm, p.status)) {
           ok = false;
           break;
         }
         fence_tc_after();
-        const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + buf * (2 * TC_BN);
+        const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + buf * acc_w;
 #pragma unroll 1
         for (int cc = half; cc < TC_BN / 32; cc += 2) {
           const int j0 = tile.z + cc * 32;
@@ -633,6 +639,10 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vect
     return real_a ? launch_bn<64, true, true>(mA, mB, p.ntiles, p, s, kclass)
                   : launch_bn<64, true, false>(mA, mB, p.ntiles, p, s, kclass);
   }
+  if (bn == 256) {  // real A only (a complex A at BN = 256 leaves too few stages)
+    if (!real_a) return cudaErrorInvalidValue;
+    return launch_bn<256, false, true>(mA, mB, p.ntiles, p, s, kclass);
+  }
   if (bn == 64)
     return real_a ? launch_bn<64, false, true>(mA, mB, p.ntiles, p, s, kclass)
                   : launch_bn<64, false, false>(mA, mB, p.ntiles, p, s, kclass);
@@ -663,15 +673,17 @@ size_t fg_tc_scratch_bytes(int64_t N, int64_t B, int64_t groups, int) {
   return (size_t)(row_tiles * col_tiles) * sizeof(int4) + 256;
 }
 
-void fg_tc_grouped_tiles(int64_t N, int64_t groups, const int64_t* gstart, const int64_t* gcount,
+int fg_tc_grouped_bn(bool real_a) { return real_a ? 256 : TC_BN_STD; }
+
+void fg_tc_grouped_tiles(int64_t N, int64_t groups, const int64_t* gstart, const int64_t* gcount, int bn,
                          std::vector<int4>& tiles) {
   tiles.clear();
   const int row_tiles = (int)((N + TC_BM - 1) / TC_BM);
   for (int64_t g = 0; g < groups; ++g) {
     const int64_t c0 = gstart[g], c1 = gstart[g] + gcount[g];
     for (int rt = 0; rt < row_tiles; ++rt)
-      for (int64_t c = c0; c < c1; c += TC_BN_MAX)
-        tiles.push_back(make_int4(rt, (int)(4 * g), (int)c, (int)std::min<int64_t>(c + TC_BN_MAX, c1)));
+      for (int64_t c = c0; c < c1; c += bn)
+        tiles.push_back(make_int4(rt, (int)(4 * g), (int)c, (int)std::min<int64_t>(c + bn, c1)));
   }
 }
 
@@ -681,17 +693,19 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
     cudaError_t e = fg_split_signals(a.X, a.B, a.N, a.Np, a.xs_rows, a.Xs, a.col_exp, s, a.bimag, a.x_real);
     if (e != cudaSuccess) return e;
   }
+  // real operators: 256-column tiles halve the re-reads of each operator tile from L2
+  const int bn = fg_tc_grouped_bn(a.real_a);
   CUtensorMap mA, mB;
   if (!make_map(&mA, a.Qs, a.N, a.N, a.Np, 4 * a.groups, a.plane_elems, TC_BM) ||
-      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN_MAX))
+      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, bn))
     return cudaErrorInvalidValue;
   std::vector<int4> tiles;
   TcParams p{};
-  if (a.tiles_dev) {  // uploaded by the caller at the start of the call
+  if (a.tiles_dev) {  // uploaded by the caller at the start of the call (built with the same bn)
     p.tiles = a.tiles_dev;
     p.ntiles = (int)a.ntiles;
   } else {
-    fg_tc_grouped_tiles(a.N, a.groups, a.gstart, a.gcount, tiles);
+    fg_tc_grouped_tiles(a.N, a.groups, a.gstart, a.gcount, bn, tiles);
   }
   p.nblk = 1;
   p.grouped = 1;
@@ -702,7 +716,7 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   p.status = a.status;
   p.bimag = a.bimag;
   p.y_real = a.y_real ? 1 : 0;
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, 128, false, a.real_a);
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, bn, false, a.real_a);
 }
 
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
@@ -712,13 +726,13 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   CUtensorMap mA, mB;
   const int64_t nplanes = 4 * (int64_t)(std::max(a.b0 + a.nb_pow, a.p_blk + 1));
   if (!make_map(&mA, a.stack, a.N, a.N, a.Np, nplanes, a.plane_elems, TC_BM) ||
-      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN_MAX))
+      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN_STD))
     return cudaErrorInvalidValue;
   std::vector<int4> tiles;
   const int row_tiles = (int)((a.N + TC_BM - 1) / TC_BM);
   for (int rt = 0; rt < row_tiles; ++rt)
-    for (int64_t c = 0; c < a.B; c += TC_BN_MAX)
-      tiles.push_back(make_int4(rt, 0, (int)c, (int)std::min<int64_t>(c + TC_BN_MAX, a.B)));
+    for (int64_t c = 0; c < a.B; c += TC_BN_STD)
+      tiles.push_back(make_int4(rt, 0, (int)c, (int)std::min<int64_t>(c + TC_BN_STD, a.B)));
   TcParams p{};
   p.nblk = a.nb_pow + (a.p_blk >= 0 ? 1 : 0);
   p.grouped = 0;

@@ -24,7 +24,9 @@ struct fgfrft_plan_s {
   float2* c64;         // [nblk][blk_elems] or NULL
   __half* f16;         // [nblk][4][plane_elems] or NULL; planes re_hi, re_lo, im_hi, im_lo
   __half* f16T;        // entry-major copy [4][N*N][Kp] or NULL (fused multi-order assembly)
-  __half* h16;         // half stack [L_max + 2][4][plane_elems]: M_0 .. M_L_max, then P; or NULL
+  float* h32;          // half stack [L_max + 2][re, im][hplane]: M_0 .. M_L_max, then P; or NULL
+  int nt;              // 64 x 64 tiles per dimension of the half stack
+  int64_t hplane;      // floats per half-stack plane (nt * nt * 4096)
   int64_t Kp;          // entry-major row pitch (nblk rounded up to 8)
   int64_t planeT;      // entries per entry-major plane (padded to 128)
   int r_neg1;
@@ -202,12 +204,14 @@ cudaError_t fg_store_block(int64_t N, const double2* M, bool conj_transpose, flo
                            int64_t Np, int64_t plane_elems, cudaStream_t s);
 cudaError_t fg_entry_major(const __half* f16, int nblk, int64_t N, int64_t Np, int64_t plane_elems, __half* T,
                            int64_t Kp, int64_t planeT, cudaStream_t s);
+// One half-stack block (FP32 re/im planes of 64 x 64 swizzled tiles) from an FP64 matrix.
+cudaError_t fg_store_half(int64_t N, const double2* M, float* planes, int nt, int64_t hplane, cudaStream_t s);
 
 // assemble.cu
-// One order from the half stack (blocks M_0..M_L_max and P, split fp16 planes): Q = e^{j pi a} P
+// One order from the half stack (blocks M_0..M_L_max and P, FP32 tiled planes): Q = e^{j pi a} P
 // + sum_{|l| <= L} c_l M_l with M_{-l} = M_l^H read as transposed tiles.  coef = [2L+2] as
 // fg_coeffs writes it.  c64 output Q [N][N] or split output Qs (pitch Np, plane stride q_plane).
-cudaError_t fg_assemble_half(const __half* planes, int64_t plane_elems, int L_max, int L, bool cplx, bool has_p,
+cudaError_t fg_assemble_half(const float* planes, int64_t hplane, int nt, int L_max, int L, bool cplx, bool has_p,
                              int64_t N, int64_t Np, const float2* coef, float2* Q, __half* Qs, int64_t q_plane,
                              bool write_im, uint32_t* status, cudaStream_t s);
 // Q (c64, [NN]) or, with Qs != NULL, split fp16 planes of N rows x Np (plane stride plane_elems).

@@ -218,6 +218,24 @@ __global__ void __launch_bounds__(256) store_block_kernel(int64_t N, const doubl
   }
 }
 
+// Half-stack block in FP32 64 x 64 tiles: planes re, im of [nt x nt tiles][64][64], tiles in
+// row-major order, element (r, c) of a tile at r * 64 + (c ^ (r & 31)) so that a warp reading
+// one row or one column of a tile hits 32 different banks.  Entries past N are zero.
+__global__ void __launch_bounds__(256) store_half_kernel(int64_t N, const double2* __restrict__ M, int nt,
+                                                         float* __restrict__ planes, int64_t hplane) {
+  const int ti = blockIdx.y, tk = blockIdx.x;
+  float* re = planes + ((int64_t)ti * nt + tk) * 4096;
+  float* im = re + hplane;
+  for (int e = threadIdx.x; e < 4096; e += blockDim.x) {
+    const int r = e >> 6, c = e & 63;
+    const int64_t i = (int64_t)ti * 64 + r, k = (int64_t)tk * 64 + c;
+    const double2 v = (i < N && k < N) ? M[i * N + k] : make_double2(0.0, 0.0);
+    const int o = r * 64 + (c ^ (r & 31));
+    re[o] = (float)v.x;
+    im[o] = (float)v.y;
+  }
+}
+
 // Entry-major copy of the split stack: T[p][e][b] = F16[b][p][e / N][e % N] for the
 // stored blocks b < nblk (e = i * N + k).  32 entries x 32 blocks per tile, staged in
 // shared memory so both the reads (along entries) and the writes (along blocks) are
@@ -317,6 +335,13 @@ cudaError_t fg_store_block(int64_t N, const double2* M, bool conj_transpose, flo
                            int64_t plane_elems, cudaStream_t s) {
   dim3 grid((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32));
   store_block_kernel<<<grid, 256, 0, s>>>(N, M, conj_transpose ? 1 : 0, c64, f16, Np, plane_elems);
+  fg_note_launch(FGFRFT_KC_OFFLINE);
+  return cudaGetLastError();
+}
+
+cudaError_t fg_store_half(int64_t N, const double2* M, float* planes, int nt, int64_t hplane, cudaStream_t s) {
+  dim3 grid((unsigned)nt, (unsigned)nt);
+  store_half_kernel<<<grid, 256, 0, s>>>(N, M, nt, planes, hplane);
   fg_note_launch(FGFRFT_KC_OFFLINE);
   return cudaGetLastError();
 }

@@ -37,8 +37,10 @@ struct TcGroupedArgs {
   bool y_real;             // write only the real parts (the caller knows the products are real)
 };
 cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s);
-// Tile table of the grouped GEMM: {row tile, plane base of Q_g, first column, end column}.
-void fg_tc_grouped_tiles(int64_t N, int64_t groups, const int64_t* gstart, const int64_t* gcount,
+// Column-tile width of the grouped GEMM (256 for real operators, else 128) and its tile table:
+// {row tile, plane base of Q_g, first column, end column}.
+int fg_tc_grouped_bn(bool real_a);
+void fg_tc_grouped_tiles(int64_t N, int64_t groups, const int64_t* gstart, const int64_t* gcount, int bn,
                          std::vector<int4>& tiles);
 
 // Y[:, j] = sum_b coef[b][j] A_b X[:, j] over the stored blocks (stacked path),

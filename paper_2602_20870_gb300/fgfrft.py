@@ -20,7 +20,7 @@ from .build import LIB
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_NOT_UNITARY, ERR_AMBIGUOUS_SPECTRUM = 1, 2, 3, 4
 ERR_NO_MEMORY, ERR_CUDA, ERR_TIMEOUT = 5, 6, 7
-STORE_C64, STORE_SPLIT_F16, STORE_ENTRY_F16, STORE_HALF_F16 = 1, 2, 4, 8
+STORE_C64, STORE_SPLIT_F16, STORE_ENTRY_F16, STORE_HALF = 1, 2, 4, 8
 ADJOINT, SHARED_ALPHA = 1, 2
 REAL_SIGNALS, REAL_OUTPUT = 0x100, 0x200
 PATH_PLAIN, PATH_ASSEMBLED, PATH_STACKED, PATH_STACKED_FP32 = 0x10, 0x20, 0x40, 0x80
@@ -213,6 +213,15 @@ class Plan:
             raise FGFRFTError(ERR_INVALID_ARG, "fgfrft_plan_block")
         base = self.mem.data_ptr()
         off = ptr - base
+        if storage == STORE_HALF:
+            # two FP32 planes of 64 x 64 tiles; element (r, c) of a tile at r * 64 + (c ^ (r & 31))
+            nt = (self.N + 63) // 64
+            planes = self.mem[off:off + stride.value * 4].view(torch.float32).view(2, nt, nt, 64, 64)
+            r = torch.arange(64, device=planes.device)
+            idx = (r[None, :] ^ (r[:, None] & 31)).expand(2, nt, nt, 64, 64)
+            tiles = torch.gather(planes, 4, idx)
+            full = tiles.permute(0, 1, 3, 2, 4).reshape(2, nt * 64, nt * 64)[:, :self.N, :self.N]
+            return torch.complex(full[0], full[1])
         if storage == STORE_C64:
             nbytes = self.N * self.N * 8
             return self.mem[off:off + nbytes].view(torch.complex64).view(self.N, self.N)

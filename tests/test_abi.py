@@ -53,8 +53,9 @@ def test_plan_bytes_layout(lib):
     plane = -(-(N * Np) // 128) * 128
     c64 = -(-((2 * L + 2) * (-(-(N * N) // 32) * 32) * 8) // 256) * 256
     assert f(N, L, 3) == 256 + c64 + -(-((2 * L + 2) * 4 * plane * 2) // 256) * 256
-    # half stack: M_0..M_L and P, L + 2 blocks of split planes
-    assert f(N, L, 8) == 256 + -(-((L + 2) * 4 * plane * 2) // 256) * 256
+    # half stack: M_0..M_L and P, L + 2 blocks of two FP32 planes of 64 x 64 tiles
+    nt = -(-N // 64)
+    assert f(N, L, 8) == 256 + -(-((L + 2) * 2 * nt * nt * 4096 * 4) // 256) * 256
     assert f(0, L, 1) == 0 and f(N, -1, 1) == 0 and f(N, L, 0) == 0 and f(N, L, 16) == 0 and f(N, L, 4) == 0
 
 

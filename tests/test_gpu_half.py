@@ -45,7 +45,7 @@ OPERATORS = {
 def case(request, FG):
     F = OPERATORS[request.param]()
     L_max = 9
-    plan = FG.Plan(F, L_max, storage=FG.STORE_HALF_F16)
+    plan = FG.Plan(F, L_max, storage=FG.STORE_HALF)
     full = FG.Plan(F, L_max, storage=FG.STORE_C64 | FG.STORE_SPLIT_F16)
     return request.param, F, O.projector(F), plan, full
 
@@ -85,12 +85,12 @@ def test_apply_paths_half(case):
 
 def test_half_stack_blocks_and_unsupported_paths(FG):
     F = W.tiny().F
-    plan = FG.Plan(F, 5, storage=FG.STORE_HALF_F16)
-    full = FG.Plan(F, 5, storage=FG.STORE_SPLIT_F16)
-    for l in (0, 3, 6):  # 6 = L_max + 1 is P
-        assert torch.equal(plan.block(l, FG.STORE_HALF_F16), full.block(l, FG.STORE_SPLIT_F16))
+    plan = FG.Plan(F, 5, storage=FG.STORE_HALF)
+    full = FG.Plan(F, 5, storage=FG.STORE_C64)
+    for l in (0, 3, 6):  # 6 = L_max + 1 is P: the same FP32 rounding of the same FP64 block
+        assert torch.equal(plan.block(l, FG.STORE_HALF), full.block(l, FG.STORE_C64))
     with pytest.raises(FG.FGFRFTError):
-        plan.block(-2, FG.STORE_HALF_F16)
+        plan.block(-2, FG.STORE_HALF)
     X = torch.zeros((4, 64), dtype=torch.complex64, device="cuda")
     for path in ("stacked", "stacked_fp32"):
         with pytest.raises(FG.FGFRFTError) as e:
@@ -103,7 +103,7 @@ def test_half_image_graph_size(FG):
     full-storage assembly (whose parity with the oracle is tested at this size elsewhere)
     and against the oracle's action on a few columns."""
     wl = W.image_graph(n_orders=2, per_order=2)
-    plan = FG.Plan(wl.F, 32, storage=FG.STORE_HALF_F16 | FG.STORE_C64)
+    plan = FG.Plan(wl.F, 32, storage=FG.STORE_HALF | FG.STORE_C64)
     a = [0.37, -1.61]
     Q = plan.assemble(a, 32)
     full = FG.Plan(wl.F, 32, storage=FG.STORE_C64)
