@@ -10,8 +10,10 @@ One step = the whole online path for that batch through the C ABI
 (fgfrft_apply on 16384 columns in 64 runs of equal order): per-order
 coefficients, one fused pass over the stored powers that assembles all 64
 operators (split-fp16), the signal split, and one tcgen05 GEMM over the 64
-groups.  The offline precompute (FP64 powers and projector) is not timed
-(the paper times only the online phase).
+groups.  The signals are real, so they are passed as real float32 arrays
+(FGFRFT_REAL_SIGNALS; real float32 outputs too when every Q is real); the same
+step on complex64 buffers is reported beside it.  The offline precompute (FP64
+powers and projector) is not timed (the paper times only the online phase).
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
 the same workload (a bounded sample of orders per step) instead.
@@ -269,9 +271,21 @@ def run_ours(args):
     X = torch.as_tensor(wl.X, dtype=torch.complex64).cuda()
     Y = torch.empty_like(X)
     stream = torch.cuda.current_stream()
+    # The signals are real (GRF fields): they are kept as real float32 and the library's
+    # real-signal interface reads them (and writes real outputs when Q is real).  The same
+    # step on complex64 buffers is timed below for comparison.
+    real_x = not bool(np.any(wl.X.imag))
+    real_q = plan.real and plan.r_neg1 == 0  # every assembled Q_g is real
+    real_out = real_x and real_q
+    if real_x:
+        Xr = torch.as_tensor(wl.X.real, dtype=torch.float32).cuda()
+        Yr = torch.empty(Xr.shape, dtype=torch.float32 if real_out else torch.complex64, device=Xr.device)
 
-    def step(path="auto"):
-        plan.apply(alpha, X, L, path=path, out=Y)
+    def step(path="auto", complex_io=False):
+        if real_x and not complex_io and path != "plain":
+            plan.apply(alpha, Xr, L, path=path, out=Yr, real_io=True, real_output=real_out)
+        else:
+            plan.apply(alpha, X, L, path=path, out=Y)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -301,19 +315,32 @@ def run_ours(args):
     t_max = reduce_max(total_ms)
     ms_step = t_max / args.steps
     value = whole_job_rate(n_orders * args.steps, ws, t_max / 1e3)
+    # the same step on complex64 device buffers
+    for _ in range(3):
+        step(complex_io=True)
+    torch.cuda.synchronize()
+    e0c, e1c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0c.record(stream)
+    for _ in range(args.steps):
+        step(complex_io=True)
+    e1c.record(stream)
+    torch.cuda.synchronize()
+    ms_step_c = reduce_max(e0c.elapsed_time(e1c)) / args.steps
+    if real_x:
+        Y.copy_(Yr)  # the result checked against the oracle: the real-signal step's output
 
     # ---- dominant kernel and its roofline (live CUDA events around each launch)
     peaks, peak_src = measured_peaks()
-    real_q = plan.real and plan.r_neg1 == 0  # every assembled Q_g is real
-    real_x = not bool(np.any(wl.X.imag))     # real signals: the real-B tensor-core products
     rooflines = {}
     if kt["tc_gemm"][1]:
         avg_ms = kt["tc_gemm"][2] / kt["tc_gemm"][1]
         # Q_g X_g over the groups: flops per (i, j, k) = 8 complex x complex, 4 real x complex,
         # 2 real x real
         flops = (2.0 if real_q and real_x else 4.0 if (real_q or real_x) else 8.0) * N * N * B
-        # bytes: split Q planes read + split X planes read + Y written
-        byts = ((4.0 if real_q else 8.0) * n_orders * N * N + (4.0 if real_x else 8.0) * B * N + 8.0 * B * N)
+        # bytes: split Q planes read + split X planes read + Y written (real float32 outputs
+        # when both are real)
+        byts = ((4.0 if real_q else 8.0) * n_orders * N * N + (4.0 if real_x else 8.0) * B * N +
+                (4.0 if real_out else 8.0) * B * N)
         tpeak = peaks.get("bf16_tflops_sustained", 1700.0)  # fp16 dense tensor rate = bf16
         hpeak = peaks.get("hbm_gbs", 6800.0)
         tflops = flops / (avg_ms * 1e-3) / 1e12
@@ -402,31 +429,29 @@ def run_ours(args):
                    "d2h_bytes_per_step": nbytes}
     # the signals are real: the same calls with real float32 host buffers (and real outputs
     # when Q is real), half the bytes over the host link
-    real_x = not bool(np.any(wl.X.imag))
     e2e_mode = "pipelined (copies of step k+1 / k-1 overlap the transform of step k), complex64 host buffers"
     if real_x:
-        real_out = plan.real and plan.r_neg1 == 0
-        Xr = torch.as_tensor(wl.X.real, dtype=torch.float32).pin_memory()
-        Yr = torch.empty(Xr.shape, dtype=torch.float32 if real_out else torch.complex64).pin_memory()
-        pipe_r = FG.Pipeline(plan, tuple(Xr.shape), L, real_io=True, real_output=real_out)
+        Xrh = torch.as_tensor(wl.X.real, dtype=torch.float32).pin_memory()
+        Yrh = torch.empty(Xrh.shape, dtype=torch.float32 if real_out else torch.complex64).pin_memory()
+        pipe_r = FG.Pipeline(plan, tuple(Xrh.shape), L, real_io=True, real_output=real_out)
         for _ in range(3):
-            pipe_r.submit(alpha, Xr, Yr)
+            pipe_r.submit(alpha, Xrh, Yrh)
         pipe_r.wait()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            pipe_r.submit(alpha, Xr, Yr)
+            pipe_r.submit(alpha, Xrh, Yrh)
         pipe_r.wait()
         e2e_s = reduce_max(time.perf_counter() - t0)
         e2e_value = whole_job_rate(n_orders * args.steps, ws, e2e_s)
         t0 = time.perf_counter()
         for _ in range(k_serial):
-            plan.apply(alpha, Xr, L, out=Yr, real_io=True, real_output=real_out)
+            plan.apply(alpha, Xrh, L, out=Yrh, real_io=True, real_output=real_out)
             torch.cuda.synchronize()
         e2e_serial = n_orders * k_serial / (time.perf_counter() - t0)
-        nbytes_in = Xr.numel() * 4
-        nbytes_out = Yr.numel() * Yr.element_size()
+        nbytes_in = Xrh.numel() * 4
+        nbytes_out = Yrh.numel() * Yrh.element_size()
         e2e_mode = ("pipelined (copies of step k+1 / k-1 overlap the transform of step k), real float32 host "
                     "signals" + (" and outputs (Q is real)" if real_out else ", complex64 outputs"))
     else:
@@ -438,9 +463,12 @@ def run_ours(args):
         "dtype": "fp16x3-split tensor GEMM, f32 accumulate; f32 assembly", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "L": L, "orders": n_orders, "signals_per_order": B // n_orders,
                    "path": "assembled (fused multi-order assembly + tcgen05 grouped GEMM)",
+                   "signals": ("real float32 signals and outputs (FGFRFT_REAL_SIGNALS / _REAL_OUTPUT)"
+                               if real_out else "real float32 signals" if real_x else "complex64 signals"),
                    "l2": "inputs larger than L2 (stack 545 MB c64 + assembled operators 537 MB per step)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "signals_per_s": whole_job_rate(B * args.steps, ws, t_max / 1e3),
+        "complex64_buffers": {"ms_per_step": ms_step_c, "value": n_orders / (ms_step_c / 1e3) * ws},
         "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99))},
         "plain_fp32": {"ms_per_step": plain_ms, "order_updates_per_s": n_orders / (plain_ms / 1e3),
                        "speedup_vs_plain": plain_ms / ms_step,

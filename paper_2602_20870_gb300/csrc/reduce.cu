@@ -89,7 +89,10 @@ __device__ __forceinline__ int split_exponent(float m) {
   return e;
 }
 
-// Four consecutive entries k0..k0+3 of one column into the four planes (8-byte stores).
+// Four consecutive entries k0..k0+3 of one column into the four planes (8-byte stores);
+// RE_ONLY: the real planes only (the caller knows the imaginary parts are zero and that no
+// reader loads the imaginary planes).
+template <bool RE_ONLY = false>
 __device__ __forceinline__ void split_store4(const float2 (&v)[4], int e, __half* r_hi, int64_t plane,
                                              int64_t k0) {
   __align__(8) __half rh[4], rl[4], ih[4], il[4];
@@ -106,8 +109,10 @@ __device__ __forceinline__ void split_store4(const float2 (&v)[4], int e, __half
   }
   *reinterpret_cast<uint2*>(r_hi + k0) = *reinterpret_cast<const uint2*>(rh);
   *reinterpret_cast<uint2*>(r_hi + plane + k0) = *reinterpret_cast<const uint2*>(rl);
-  *reinterpret_cast<uint2*>(r_hi + 2 * plane + k0) = *reinterpret_cast<const uint2*>(ih);
-  *reinterpret_cast<uint2*>(r_hi + 3 * plane + k0) = *reinterpret_cast<const uint2*>(il);
+  if (!RE_ONLY) {
+    *reinterpret_cast<uint2*>(r_hi + 2 * plane + k0) = *reinterpret_cast<const uint2*>(ih);
+    *reinterpret_cast<uint2*>(r_hi + 3 * plane + k0) = *reinterpret_cast<const uint2*>(il);
+  }
 }
 
 // Block-wide max over 256 threads (every thread gets the result).
@@ -200,8 +205,8 @@ __global__ void grad_final_kernel(const double* __restrict__ partial, int nchunk
 // imaginary part.
 // G > 0: each thread keeps its G groups of 4 consecutive entries in registers between
 // the max and the split (one read of the column; needs Np <= 1024 G).  G == 0: any Np,
-// the column is read twice.  XR: the signals are real float32 (B x N), the imaginary
-// parts zero.
+// the column is read twice.  XR: the signals are real float32 (B x N); the imaginary planes
+// are not written (the flag stays 0, so the GEMM reads only the real planes).
 template <int G, bool XR>
 __global__ void __launch_bounds__(256) split_signals_kernel(const void* __restrict__ Xv, int64_t B, int64_t N,
                                                             int64_t Np, int64_t rows_pad, __half* __restrict__ planes,
@@ -243,7 +248,7 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const void* __restri
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int64_t k0 = 4 * ((int64_t)threadIdx.x + (int64_t)g * blockDim.x);
-      if (k0 < Np) split_store4(v[g], e, r_hi, plane, k0);  // Np is a multiple of 8
+      if (k0 < Np) split_store4<XR>(v[g], e, r_hi, plane, k0);  // Np is a multiple of 8
     }
   } else {
     for (int64_t k = threadIdx.x; k < N; k += blockDim.x) {
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const void* __restri
       float2 v[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) v[u] = k0 + u < N ? load(k0 + u) : make_float2(0.f, 0.f);
-      split_store4(v, e, r_hi, plane, k0);
+      split_store4<XR>(v, e, r_hi, plane, k0);
     }
   }
 }
