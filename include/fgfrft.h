@@ -263,6 +263,14 @@ int fgfrft_timing_enable(int on);
 int fgfrft_timing_reset(void);
 int fgfrft_timing_read(int kernel_class, int64_t* launches, int64_t* timed_calls, double* total_ms);
 
+/* Failure-path check: launches one CTA whose bounded device wait (the helper every
+ * kernel uses, limit 2 s) waits on an mbarrier that nothing completes.  The wait runs
+ * out, FGFRFT_ERR_TIMEOUT is recorded in the plan's status word exactly as for a stalled
+ * kernel (read and cleared by fgfrft_plan_status), and the kernel returns; nothing faults
+ * and the context stays usable.  For tests of the error path.  No counterpart in the
+ * paper. */
+int fgfrft_check_wait_timeout(fgfrft_plan p, void* stream);
+
 /*
  * Zero-allocation alpha-gradient: gradalpha[j] = Re sum_i conj(G_ij) D_ij for
  * j < B, the same quantity fgfrft_grad returns in gradalpha_dev, for callers that

@@ -53,6 +53,7 @@ SIGNATURES = {
     "fgfrft_timing_reset": (_i32, []),
     "fgfrft_timing_read": (_i32, [_i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_dp)]),
     "fgfrft_grad_alpha_noalloc": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp]),
+    "fgfrft_check_wait_timeout": (_i32, [_vp, _vp]),
 }
 
 NOALLOC_MAX_PARTIALS = 65536
@@ -229,6 +230,12 @@ class Plan:
         pe = stride.value // 4
         planes = self.mem[off:off + stride.value * 2].view(torch.float16).view(4, pe)
         return planes[:, : self.N * Np].reshape(4, self.N, Np)[:, :, : self.N]
+
+    def check_wait_timeout(self, stream=None):
+        """Run the bounded-wait failure path once (fgfrft_check_wait_timeout); the next
+        ``status()`` reports FGFRFT_ERR_TIMEOUT."""
+        _check(_lib().fgfrft_check_wait_timeout(self._h, ctypes.c_void_p(_stream(stream))),
+               "fgfrft_check_wait_timeout")
 
     def status(self, stream=None):
         _check(_lib().fgfrft_plan_status(self._h, ctypes.c_void_p(_stream(stream))), "fgfrft_plan_status")
