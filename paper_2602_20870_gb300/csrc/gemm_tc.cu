@@ -97,6 +97,7 @@ struct TcParams {
   int smem_bytes;     // dynamic shared memory usable from the 1024-aligned base
   float uscale;       // nonzero: every column has this output scale (no per-column exponents)
   int y_real;         // grouped output: Y is real float32 (only the real parts are written)
+  int cps;            // k-chunks per ring stage (one mbarrier handshake per group of chunks)
   const int* bimag;   // NULL, or a device word that is 0 when every B column is real
   const float2* coef;
   const float2* coefd;
@@ -220,7 +221,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* const bres = sbase + sizeof(TcCtl);  // resident B: [chunk][4 planes][BN rows x 64 B]
   const int res_bytes = RB ? p.kchunks * 4 * TC_PLANE_B : 0;
   uint8_t* const stages = bres + res_bytes;
-  const int stage_bytes = A_PLANES * TC_PLANE_A + (RB ? 0 : nbp * TC_PLANE_B);
+  const int chunk_bytes = A_PLANES * TC_PLANE_A + (RB ? 0 : nbp * TC_PLANE_B);
+  const int cps = p.cps > 1 ? p.cps : 1;
+  const int stage_bytes = cps * chunk_bytes;
   const int nst = min(TC_MAXST, (p.smem_bytes - (int)sizeof(TcCtl) - res_bytes) / stage_bytes);
   // TMEM columns of one accumulator buffer, and how many buffers fit (2: the epilogue of one
   // block overlaps the MMAs of the next)
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (t + (int)gridDim.x < p.ntiles) next = tile_of(p, t + gridDim.x);  // prefetch
         for (int b = 0; ok && b < p.nblk; ++b) {
           const int zA = p.grouped ? tile.y : 4 * (b < p.nb_pow ? p.b0 + b : p.p_blk);
-          for (int kc = 0; kc < p.kchunks; ++kc) {
+          for (int kc0 = 0; kc0 < p.kchunks; kc0 += cps) {
             const int s = s_cur;
             const uint32_t ph = ph_cur;
             if (++s_cur == nst) {
@@ -286,16 +289,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(&sm.full[s], (uint32_t)stage_bytes);
+            const int nc = min(cps, p.kchunks - kc0);
+            mbar_arrive_expect_tx(&sm.full[s], (uint32_t)(nc * chunk_bytes));
             issued[s]++;
-            uint8_t* st = stages + s * stage_bytes;
-            const int k0 = kc * TC_KC;
+            for (int c = 0; c < nc; ++c) {
+              uint8_t* st = stages + s * stage_bytes + c * chunk_bytes;
+              const int k0 = (kc0 + c) * TC_KC;
 #pragma unroll
-            for (int q = 0; q < A_PLANES; ++q)
-              tma_load_3d(st + q * TC_PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
-            if (!RB) {
-              for (int q = 0; q < nbp; ++q)
-                tma_load_3d(st + A_PLANES * TC_PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
+              for (int q = 0; q < A_PLANES; ++q)
+                tma_load_3d(st + q * TC_PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
+              if (!RB) {
+                for (int q = 0; q < nbp; ++q)
+                  tma_load_3d(st + A_PLANES * TC_PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
+              }
             }
           }
         }
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           fence_tc_after();
           const uint32_t d_re = tmem + buf * acc_w;
           const uint32_t d_im = d_re + TC_BN;
-          for (int kc = 0; kc < p.kchunks; ++kc) {
+          for (int kc0 = 0; kc0 < p.kchunks; kc0 += cps) {
             const int s = s_cur;
             const uint32_t ph = ph_cur;
             if (++s_cur == nst) {
@@ -344,7 +350,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               break;
             }
             fence_tc_after();
-            const uint32_t sa = smem_u32(stages + s * stage_bytes);
+            const int nc = min(cps, p.kchunks - kc0);
+            for (int c = 0; c < nc; ++c) {
+            const int kc = kc0 + c;
+            const uint32_t sa = smem_u32(stages + s * stage_bytes + c * chunk_bytes);
             const uint32_t sb = RB ? smem_u32(bres + kc * 4 * TC_PLANE_B) : sa + A_PLANES * TC_PLANE_A;
 #pragma unroll
             for (int kk = 0; kk < TC_KC / 16; ++kk) {
@@ -381,6 +390,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 umma(d_im, ail, brh, kIdesc, 1);
               }
             }
+            }                           // chunks of the stage
             umma_commit(&sm.empty[s]);  // stage s is free once these MMAs complete
           }
           if (!ok) break;
@@ -604,7 +614,7 @@ cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, int ntiles, 
   const int smem = smem_optin();
   using Cfg = TcCfg<BN, RB, RA>;
   const int res_bytes = RB ? p.kchunks * 4 * Cfg::PLANE_B : 0;
-  const int worst_stage = Cfg::A_PLANES * TC_PLANE_A + (RB ? 0 : 4 * Cfg::PLANE_B);
+  const int worst_stage = (p.cps > 1 ? p.cps : 1) * (Cfg::A_PLANES * TC_PLANE_A + (RB ? 0 : 4 * Cfg::PLANE_B));
   TcParams q = p;
   q.smem_bytes = smem - 1024;  // the kernel aligns its base up to 1024 bytes
   if (q.smem_bytes - (int)sizeof(TcCtl) - res_bytes < TC_MIN_STAGES * worst_stage) return cudaErrorInvalidValue;
@@ -791,6 +801,15 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   p.uscale = ldexpf(1.0f, a.Qs ? -FG_COEF_EXP : -(FG_SPLIT_SHIFT + FG_COEF_EXP));
   // one column tile (A <= 64): the coefficient operand stays resident in shared memory
   const bool rb = bn == 64 && p.kchunks <= TC_RB_MAXCH;
+  // the k-chunks of a tile are few (K = 2L+2 stored blocks): group them into one ring stage,
+  // as many as leave room for two stages
+  {
+    const int plane_b = bn * TC_KC * 2;
+    const int chunk = (a.real_a ? 2 : 4) * TC_BM * TC_KC * 2 + (rb ? 0 : 4 * plane_b);
+    const int res = rb ? p.kchunks * 4 * plane_b : 0;
+    const int avail = smem_optin() - 1024 - (int)sizeof(TcCtl) - res;
+    p.cps = std::max(1, std::min(p.kchunks, avail / (2 * chunk)));
+  }
   return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, bn, rb, a.real_a);
 }
 
