@@ -68,8 +68,8 @@ struct __align__(1024) TcCtl {
   uint64_t full[TC_MAXST];
   uint64_t empty[TC_MAXST];
   uint64_t bfull;
-  uint64_t tfull[2];
-  uint64_t tempty[2];
+  uint64_t tfull[4];
+  uint64_t tempty[4];
   uint64_t drain;
   uint32_t tmem_base;
   volatile int abort;
@@ -228,16 +228,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // TMEM columns of one accumulator buffer, and how many buffers fit (2: the epilogue of one
   // block overlaps the MMAs of the next)
   const uint32_t acc_w = (re_only ? 1u : 2u) * (uint32_t)BN;
-  const int nbuf = (uint32_t)Cfg::TMEM_COLS >= 2 * acc_w ? 2 : 1;
+  // ping-pong epilogue (one block per tile and one output scale, as in the fused assembly):
+  // the two epilogue warp groups take alternate tiles, with up to four accumulator buffers
+  // so the MMAs run ahead of both
+  const bool pingpong = p.nblk == 1 && p.uscale != 0.f;
+  const int nbuf_fit = (int)((uint32_t)Cfg::TMEM_COLS / acc_w);
+  const int nbuf = pingpong ? min(4, nbuf_fit) : (nbuf_fit >= 2 ? 2 : 1);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; ++s) {
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 4; ++b) {
       mbar_init(&sm.tfull[b], 1);
-      mbar_init(&sm.tempty[b], TC_EPI_WARPS);
+      mbar_init(&sm.tempty[b], pingpong ? TC_EPI_WARPS / 2 : TC_EPI_WARPS);
     }
     mbar_init(&sm.drain, 1);
     mbar_init(&sm.bfull, 1);
@@ -330,7 +335,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (RB && blockIdx.x < p.ntiles) ok = tc_wait(&sm.bfull, 0, sm, p.status);
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
         for (int b = 0; ok && b < p.nblk; ++b, ++bc) {
-          const uint32_t buf = nbuf == 2 ? (bc & 1) : 0, tph = nbuf == 2 ? ((bc >> 1) & 1) : (bc & 1);
+          const uint32_t buf = bc % (uint32_t)nbuf, tph = (bc / (uint32_t)nbuf) & 1;
           if (!tc_wait(&sm.tempty[buf], tph ^ 1, sm, p.status)) {
             ok = false;
             break;
@@ -424,7 +429,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     };
     int4 next = blockIdx.x < p.ntiles ? tile_of(p, blockIdx.x) : make_int4(0, 0, 0, 0);
     float next_scale = blockIdx.x < p.ntiles ? col_scale(next) : 0.f;
-    for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
+    int64_t li = 0;  // local tile index (ping-pong: group `half` takes the tiles li = half mod 2)
+    for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++li) {
+      const bool mine = !pingpong || (int)(li & 1) == half;
       const int4 tile = next;
       const float my_scale = next_scale;
       if (t + (int)gridDim.x < p.ntiles) {
@@ -445,7 +452,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
 
       for (int b = 0; b < p.nblk; ++b, ++bc) {
-        const uint32_t buf = nbuf == 2 ? (bc & 1) : 0, tph = nbuf == 2 ? ((bc >> 1) & 1) : (bc & 1);
+        if (!mine) continue;  // the other group's tile (its buffer index still counts)
+        const uint32_t buf = bc % (uint32_t)nbuf, tph = (bc / (uint32_t)nbuf) & 1;
         if (!tc_wait(&sm.tfull[buf], tph, sm, p.status)) {
           ok = false;
           break;
@@ -453,7 +461,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         fence_tc_after();
         const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + buf * acc_w;
 #pragma unroll 1
-        for (int cc = half; cc < TC_BN / 32; cc += 2) {
+        for (int cc = pingpong ? 0 : half; cc < TC_BN / 32; cc += pingpong ? 1 : 2) {
           const int j0 = tile.z + cc * 32;
           if (j0 >= tile.w) break;  // uniform: no column of this chunk is in range
           const int ncol = min(32, tile.w - j0);
