@@ -81,6 +81,35 @@ std::vector<std::pair<int64_t, int64_t>> order_runs(const std::vector<double>& a
   return runs;
 }
 
+// The small host tables of one call (orders, tile and group tables): read by the kernels
+// straight from pinned host memory (fg_stage), or copied into the work buffer when no slot
+// is free.  The slots are released, on the call's stream, when the guard goes out of scope,
+// after every kernel of the call is enqueued.
+struct Staged {
+  cudaStream_t s;
+  int tok[8];
+  int n = 0;
+  bool failed = false;
+  explicit Staged(cudaStream_t st) : s(st) {}
+  Staged(const Staged&) = delete;
+  Staged& operator=(const Staged&) = delete;
+  ~Staged() {
+    for (int i = 0; i < n; ++i) fg_stage_done(tok[i], s);
+  }
+  // device-readable copy of src; fallback: a stream copy to dev_fallback (in the work buffer)
+  template <class T>
+  const T* put(const T* src, size_t count, T* dev_fallback) {
+    const void* dev = nullptr;
+    const int t = n < 8 ? fg_stage(src, count * sizeof(T), &dev) : -1;
+    if (t >= 0) {
+      tok[n++] = t;
+      return static_cast<const T*>(dev);
+    }
+    if (fg_h2d(dev_fallback, src, count * sizeof(T), s) != cudaSuccess) failed = true;
+    return dev_fallback;
+  }
+};
+
 // Sequential sub-allocator over a caller work buffer (nullptr base = sizing only).
 struct Carve {
   char* base;
@@ -595,8 +624,10 @@ int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, v
   cudaStream_t s = (cudaStream_t)stream;
   AssembleWork w = carve_assemble(p, (char*)work, A, L);
   if (!w.tensor && !p->c64 && !p->h32) return FGFRFT_ERR_UNSUPPORTED;
-  CK(fg_h2d(w.alpha_dev, a.data(), (size_t)A * sizeof(double), s));
-  CK(run_assemble(p, w, w.alpha_dev, A, L, (float2*)Q_dev, nullptr, s));
+  Staged st(s);
+  const double* ad = st.put(a.data(), (size_t)A, w.alpha_dev);
+  if (st.failed) return FGFRFT_ERR_CUDA;
+  CK(run_assemble(p, w, ad, A, L, (float2*)Q_dev, nullptr, s));
   return FGFRFT_OK;
 }
 
@@ -614,15 +645,17 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
   const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
   const float2* X = (const float2*)X_dev;
   float2* Y = (float2*)Y_dev;
+  Staged st(s);  // the call's host tables; released after the last launch below
   switch (path) {
     case FGFRFT_PATH_PLAIN: {
       if (!p->c64 && !(p->real && p->f16) && !p->h32) return FGFRFT_ERR_UNSUPPORTED;
       if (groups > 65535) return FGFRFT_ERR_UNSUPPORTED;
       std::vector<double> ga((size_t)groups);
       for (int64_t g = 0; g < groups; ++g) ga[(size_t)g] = a[(size_t)runs[(size_t)g].first];
-      CK(fg_h2d(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), s));
+      const double* gad = st.put(ga.data(), ga.size(), w.group_alpha_dev);
+      if (st.failed) return FGFRFT_ERR_CUDA;
       // coefficient vectors one per order, contiguous: [groups][2L+2] (and c_l' for the dual)
-      CK(fg_coeffs(w.group_alpha_dev, (int)groups, L, false, w.coef, D_dev ? w.coefd : nullptr, 1, nb + 1, s));
+      CK(fg_coeffs(gad, (int)groups, L, false, w.coef, D_dev ? w.coefd : nullptr, 1, nb + 1, s));
       // per order: stream the stack once into Q_g (one single-order assembly launch each;
       // real F streams the two real split planes), then all Q_g X_g on FP32 CUDA cores in
       // one batched launch
@@ -634,7 +667,8 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
         gt[(size_t)g] = make_int2((int)runs[(size_t)g].first, (int)runs[(size_t)g].second);
         maxc = std::max(maxc, (int)runs[(size_t)g].second);
       }
-      CK(fg_h2d(w.gtab, gt.data(), gt.size() * sizeof(int2), s));
+      const int2* gtd = st.put(gt.data(), gt.size(), w.gtab);
+      if (st.failed) return FGFRFT_ERR_CUDA;
       SimtStackArgs sa{};
       sa.A = w.Qc;
       sa.lda = n;
@@ -645,7 +679,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       sa.ncols = (int)B;
       sa.X = X;
       sa.Y = Y;
-      sa.groups = w.gtab;
+      sa.groups = gtd;
       sa.group_stride = p->N * p->N;
       sa.max_group_cols = maxc;
       sa.ngroups = (int)groups;
@@ -659,8 +693,9 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
     }
     case FGFRFT_PATH_STACKED_FP32: {
       if (!p->c64) return FGFRFT_ERR_UNSUPPORTED;
-      CK(fg_h2d(w.alpha_dev, a.data(), (size_t)B * sizeof(double), s));
-      CK(fg_coeffs(w.alpha_dev, (int)B, L, false, w.coef, D_dev ? w.coefd : nullptr, B, 1, s));
+      const double* ad = st.put(a.data(), (size_t)B, w.alpha_dev);
+      if (st.failed) return FGFRFT_ERR_CUDA;
+      CK(fg_coeffs(ad, (int)B, L, false, w.coef, D_dev ? w.coefd : nullptr, B, 1, s));
       SimtStackArgs sa{};
       sa.A = p->c64;
       sa.blk_elems = p->blk_elems;
@@ -699,14 +734,15 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       fg_tc_grouped_tiles(p->N, groups, gstart.data(), gcount.data(),
                           fg_tc_grouped_bn(p->real && p->r_neg1 == 0), tiles);
       if (tiles.size() * sizeof(int4) > w.tc_scratch_bytes) return FGFRFT_ERR_INVALID_ARG;
-      CK(fg_h2d(w.group_alpha_dev, ga.data(), ga.size() * sizeof(double), s));
-      CK(fg_h2d(w.tc_scratch, tiles.data(), tiles.size() * sizeof(int4), s));
+      const double* gad = st.put(ga.data(), ga.size(), w.group_alpha_dev);
+      const int4* tiles_dev = st.put(tiles.data(), tiles.size(), (int4*)w.tc_scratch);
+      if (st.failed) return FGFRFT_ERR_CUDA;
       if (D_dev)
-        CK(run_assemble_dual(p, w.asm_work, w.group_alpha_dev, groups, L, w.Qs, w.dQs, s));
+        CK(run_assemble_dual(p, w.asm_work, gad, groups, L, w.Qs, w.dQs, s));
       else
-        CK(run_assemble(p, w.asm_work, w.group_alpha_dev, groups, L, nullptr, w.Qs, s));
+        CK(run_assemble(p, w.asm_work, gad, groups, L, nullptr, w.Qs, s));
       TcGroupedArgs ta{};
-      ta.tiles_dev = (const int4*)w.tc_scratch;
+      ta.tiles_dev = tiles_dev;
       ta.ntiles = (int64_t)tiles.size();
       ta.N = p->N;
       ta.Np = p->Np;
@@ -739,8 +775,9 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
     }
     case FGFRFT_PATH_STACKED: {
       if (!p->f16 || !fg_tc_available()) return FGFRFT_ERR_UNSUPPORTED;
-      CK(fg_h2d(w.alpha_dev, a.data(), (size_t)B * sizeof(double), s));
-      CK(fg_coeffs(w.alpha_dev, (int)B, L, false, w.coef, D_dev ? w.coefd : nullptr, B, 1, s));
+      const double* ad = st.put(a.data(), (size_t)B, w.alpha_dev);
+      if (st.failed) return FGFRFT_ERR_CUDA;
+      CK(fg_coeffs(ad, (int)B, L, false, w.coef, D_dev ? w.coefd : nullptr, B, 1, s));
       TcStackedArgs ta{};
       ta.N = p->N;
       ta.Np = p->Np;

@@ -88,6 +88,7 @@ struct TcParams {
   int b0, nb_pow, p_blk;
   int64_t rows;       // rows of A (M extent) and the stride of output columns
   int kchunks;
+  int kvalid;         // k range with data (0: kchunks * 32); k16 steps at or past it are all zero
   // split output (fused assembly): column j, row r -> Qs[j][plane][r / qN][r % qN] (pitch qNp),
   // value scaled by 2^FG_SPLIT_SHIFT and split into fp16 hi/lo
   __half* Qs;
@@ -176,6 +177,19 @@ __device__ __forceinline__ void split_out_cols(const uint32_t (&vr)[32], const u
   const int64_t pl = p.qplane, cs = 4 * pl;
   __half* qp = p.Qs + (int64_t)j0 * cs + qoff;
   const bool write_im = !p.skip_im;
+  if (!write_im) {  // real operators: the real planes only
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      if (c < ncol) {
+        const float re = __uint_as_float(vr[c]) * (UNIFORM ? p.uscale : scale[cc * 32 + c]);
+        const __half hi = __float2half_rn(re);
+        qp[0] = hi;
+        qp[pl] = __float2half_rn(re - __half2float(hi));
+      }
+      qp += cs;
+    }
+    return;
+  }
 #pragma unroll
   for (int c = 0; c < 32; ++c) {
     if (c < ncol) {
@@ -366,6 +380,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               const uint64_t arh = desc_sw64(sa + 0 * TC_PLANE_A + off), arl = desc_sw64(sa + 1 * TC_PLANE_A + off);
               const uint64_t brh = desc_sw64(sb + 0 * TC_PLANE_B + off), brl = desc_sw64(sb + 1 * TC_PLANE_B + off);
               const uint64_t bih = desc_sw64(sb + 2 * TC_PLANE_B + off), bil = desc_sw64(sb + 3 * TC_PLANE_B + off);
+              if (p.kvalid > 0 && kc * TC_KC + kk * 16 >= p.kvalid) continue;  // all-zero k16 step
               const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
               // real part: Ar*Xr - Ai*Xi
               umma(d_re, arh, brh, kIdesc, acc);
@@ -796,6 +811,7 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   p.grouped = 1;
   p.rows = a.entries;
   p.kchunks = (int)((a.K + TC_KC - 1) / TC_KC);
+  p.kvalid = (int)a.K;
   p.Y = a.Qc;
   p.Qs = a.Qs;
   p.qN = a.N;

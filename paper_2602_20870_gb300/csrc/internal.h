@@ -176,6 +176,11 @@ bool fg_make_map_f16(CUtensorMap* m, const void* base, int64_t cols, int64_t row
 // Host-to-device copy of a small per-call table, staged through pinned memory so that the
 // call stays asynchronous (the source may be reused as soon as this returns).
 cudaError_t fg_h2d(void* dst, const void* src, size_t bytes, cudaStream_t s);
+// A pinned copy of a small table that kernels read directly from host memory: returns a
+// token (and the device-readable address in *dev), or -1 when the caller must copy instead.
+// fg_stage_done(token, s) must follow once every kernel that reads it is enqueued on s.
+int fg_stage(const void* src, size_t bytes, const void** dev);
+void fg_stage_done(int token, cudaStream_t s);
 struct FgTimed {  // records a CUDA event pair around its scope when timing is enabled
   FgTimed(int cls, cudaStream_t s);
   ~FgTimed();

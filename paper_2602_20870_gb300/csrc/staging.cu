@@ -3,10 +3,12 @@
 // cudaMemcpyAsync from pageable host memory returns only once the copy has been staged,
 // which waits for the stream to reach it: every call would then hold the host until the
 // device has drained the work queued before it, and the device would idle while the host
-// enqueues the rest of the call.  Copying through pinned memory keeps the call
-// asynchronous.  The pinned memory is a ring of fixed slots per device; a slot is reused
-// only after the copy that last read from it has run (one event per slot).  A copy larger
-// than a slot, or any copy when pinned memory is unavailable, takes the pageable route.
+// enqueues the rest of the call.  The tables therefore go to a ring of fixed pinned slots
+// per device, and the kernels read them there directly (fg_stage): a copy on the stream
+// would also queue, on the copy engine, behind large signal transfers of other streams.
+// A slot is reused only after the work that reads it has run (one event per slot, recorded
+// by fg_stage_done or after fg_h2d's copy).  A table larger than a slot, or any table when
+// pinned memory is unavailable, takes a stream copy.
 #include <cstring>
 #include <mutex>
 
@@ -20,8 +22,10 @@ constexpr int kMaxDevices = 64;
 
 struct Ring {
   char* base = nullptr;
+  char* dbase = nullptr;  // device address of base
   cudaEvent_t ev[kSlots] = {};
   bool used[kSlots] = {};
+  bool held[kSlots] = {};  // reserved by fg_stage until fg_stage_done
   int next = 0;
   bool failed = false;
 };
@@ -33,7 +37,7 @@ bool ring_init(Ring& r) {
   if (r.base) return true;
   if (r.failed) return false;
   void* p = nullptr;
-  if (cudaHostAlloc(&p, (size_t)kSlots * kSlotBytes, cudaHostAllocPortable) != cudaSuccess || !p) {
+  if (cudaHostAlloc(&p, (size_t)kSlots * kSlotBytes, cudaHostAllocPortable | cudaHostAllocMapped) != cudaSuccess || !p) {
     cudaGetLastError();
     r.failed = true;
     return false;
@@ -47,8 +51,26 @@ bool ring_init(Ring& r) {
       return false;
     }
   }
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess || !d) {
+    cudaGetLastError();
+    d = nullptr;  // fg_stage falls back to stream copies
+  }
   r.base = static_cast<char*>(p);
+  r.dbase = static_cast<char*>(d);
   return true;
+}
+
+// Next free slot of the ring (waiting for its previous reader if needed), or -1.
+int take_slot(Ring& r) {
+  for (int tries = 0; tries < kSlots; ++tries) {
+    const int k = r.next;
+    r.next = (k + 1) % kSlots;
+    if (r.held[k]) continue;
+    if (r.used[k] && cudaEventSynchronize(r.ev[k]) != cudaSuccess) return -1;
+    return k;
+  }
+  return -1;
 }
 
 }  // namespace
@@ -60,12 +82,8 @@ cudaError_t fg_h2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     std::lock_guard<std::mutex> g(g_mu);
     Ring& r = g_ring[dev];
     if (ring_init(r)) {
-      const int k = r.next;
-      r.next = (k + 1) % kSlots;
-      if (r.used[k]) {
-        const cudaError_t e = cudaEventSynchronize(r.ev[k]);  // the slot's previous copy has run
-        if (e != cudaSuccess) return e;
-      }
+      const int k = take_slot(r);
+      if (k < 0) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
       char* slot = r.base + (size_t)k * kSlotBytes;
       std::memcpy(slot, src, bytes);
       cudaError_t e = cudaMemcpyAsync(dst, slot, bytes, cudaMemcpyHostToDevice, s);
@@ -77,4 +95,34 @@ cudaError_t fg_h2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     }
   }
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+}
+
+int fg_stage(const void* src, size_t bytes, const void** dev) {
+  *dev = nullptr;
+  int d = 0;
+  if (bytes == 0 || bytes > kSlotBytes || cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return -1;
+  std::lock_guard<std::mutex> g(g_mu);
+  Ring& r = g_ring[d];
+  if (!ring_init(r) || !r.dbase) return -1;
+  const int k = take_slot(r);
+  if (k < 0) return -1;
+  std::memcpy(r.base + (size_t)k * kSlotBytes, src, bytes);
+  r.held[k] = true;
+  *dev = r.dbase + (size_t)k * kSlotBytes;
+  return d * kSlots + k;
+}
+
+void fg_stage_done(int token, cudaStream_t s) {
+  if (token < 0) return;
+  const int d = token / kSlots, k = token % kSlots;
+  if (d >= kMaxDevices) return;
+  std::lock_guard<std::mutex> g(g_mu);
+  Ring& r = g_ring[d];
+  if (!r.held[k]) return;
+  r.used[k] = cudaEventRecord(r.ev[k], s) == cudaSuccess;
+  if (!r.used[k]) {  // no event: wait for the work that reads the slot before releasing it
+    cudaGetLastError();
+    cudaStreamSynchronize(s);
+  }
+  r.held[k] = false;
 }
