@@ -272,6 +272,55 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const void* __restri
   }
 }
 
+// The same split with one warp per column (Np <= 1024, 8 columns per CTA): lane l holds
+// the groups 4(l + 32g) .. +3, g < 8, so the max needs only warp shuffles and each group's
+// plane stores are 8 bytes, 256 contiguous bytes per warp instruction.
+template <bool XR>
+__global__ void __launch_bounds__(256) split_signals_warp_kernel(const void* __restrict__ Xv, int64_t B, int64_t N,
+                                                                 int64_t Np, int64_t rows_pad,
+                                                                 __half* __restrict__ planes,
+                                                                 int* __restrict__ col_exp, int* __restrict__ bimag) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= rows_pad) return;
+  const int64_t plane = rows_pad * Np;
+  __half* r_hi = planes + j * Np;
+  if (j >= B) {  // padding rows are zero
+    for (int64_t k = lane; k < Np; k += 32) {
+      r_hi[k] = r_hi[plane + k] = r_hi[2 * plane + k] = r_hi[3 * plane + k] = __float2half(0.f);
+    }
+    return;
+  }
+  const float2* x = static_cast<const float2*>(Xv) + j * N;
+  const float* xr = static_cast<const float*>(Xv) + j * N;
+  float2 v[8][4];
+  float m = 0.f;
+  bool im = false;
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    const int64_t k0 = 4 * ((int64_t)lane + 32 * g);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = k0 + u;
+      v[g][u] = k < N ? (XR ? make_float2(xr[k], 0.f) : x[k]) : make_float2(0.f, 0.f);
+      m = fmaxf(m, fmaxf(fabsf(v[g][u].x), fabsf(v[g][u].y)));
+      im |= !(v[g][u].y == 0.f);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const bool any_im = __any_sync(0xffffffffu, im);
+  const int e = split_exponent(m);
+  if (lane == 0) {
+    col_exp[j] = e;
+    if (any_im && bimag) *bimag = 1;  // every writer stores the same value
+  }
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    const int64_t k0 = 4 * ((int64_t)lane + 32 * g);
+    if (k0 < Np) split_store4<XR>(v[g], e, r_hi, plane, k0);  // Np is a multiple of 8
+  }
+}
+
 }  // namespace
 
 cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* coef, float2* coefd, int64_t ldb,
@@ -312,6 +361,14 @@ cudaError_t fg_split_signals(const void* X, int64_t B, int64_t N, int64_t Np, in
   fg_note_launch(FGFRFT_KC_SPLIT_SIGNALS);
   const unsigned grid = (unsigned)rows_pad;
   auto go = [&](auto kern) { kern<<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag); };
+  if (Np <= 1024) {  // a warp per column
+    const unsigned g8 = (unsigned)((rows_pad + 7) / 8);
+    if (x_real)
+      split_signals_warp_kernel<true><<<g8, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
+    else
+      split_signals_warp_kernel<false><<<g8, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
+    return cudaGetLastError();
+  }
   if (x_real) {
     if (Np <= 1024) go(split_signals_kernel<1, true>);
     else if (Np <= 2048) go(split_signals_kernel<2, true>);
