@@ -370,13 +370,11 @@ cudaError_t fg_split_signals(const void* X, int64_t B, int64_t N, int64_t Np, in
     return cudaGetLastError();
   }
   if (x_real) {
-    if (Np <= 1024) go(split_signals_kernel<1, true>);
-    else if (Np <= 2048) go(split_signals_kernel<2, true>);
+    if (Np <= 2048) go(split_signals_kernel<2, true>);
     else if (Np <= 4096) go(split_signals_kernel<4, true>);
     else go(split_signals_kernel<0, true>);
   } else {
-    if (Np <= 1024) go(split_signals_kernel<1, false>);
-    else if (Np <= 2048) go(split_signals_kernel<2, false>);
+    if (Np <= 2048) go(split_signals_kernel<2, false>);
     else if (Np <= 4096) go(split_signals_kernel<4, false>);
     else go(split_signals_kernel<0, false>);
   }
