@@ -74,9 +74,10 @@ enum fgfrft_storage {
                                  of the entries scaled by 2^12, 8 B per entry:
                                  tensor-core paths */
   FGFRFT_STORE_ENTRY_F16 = 4, /* an entry-major copy of the split planes: for every entry
-                                 of the N x N blocks, all 2 L_max + 2 stored blocks
-                                 contiguous (row pitch rounded up to 8); lets the fused
-                                 multi-order assembly run as one tensor-core GEMM.
+                                 of the N x N blocks, the 2 L_max + 2 stored blocks (padded
+                                 to Kp, a multiple of 8) in chunks of 32 contiguous values
+                                 (chunk-major planes, then a Kp mod 32 tail plane); lets the
+                                 fused multi-order assembly run as one tensor-core GEMM.
                                  Requires FGFRFT_STORE_SPLIT_F16. */
   FGFRFT_STORE_HALF = 8,      /* M_0 .. M_{L_max} and P only (L_max + 2 blocks): a negative
                                  power is read as the conjugate transpose of the stored

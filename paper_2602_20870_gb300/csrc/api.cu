@@ -35,9 +35,9 @@ Layout plan_layout(int64_t N, int L_max, int storage) {
   l.off_f16 = off;
   if (storage & FGFRFT_STORE_SPLIT_F16) off = align_up(off + (size_t)nblk * 4 * l.plane_elems * sizeof(__half));
   l.Kp = round_up(nblk, 8);
-  l.planeT = round_up(N * N * l.Kp, 128);
+  l.planeT = round_up(N * N, 128);  // entries per chunk plane of the entry-major copy
   l.off_f16T = off;
-  if (storage & FGFRFT_STORE_ENTRY_F16) off = align_up(off + (size_t)4 * l.planeT * sizeof(__half));
+  if (storage & FGFRFT_STORE_ENTRY_F16) off = align_up(off + (size_t)4 * l.Kp * l.planeT * sizeof(__half));
   l.nt = (int)((N + 63) / 64);
   l.hplane = (int64_t)l.nt * l.nt * 4096;
   l.off_h16 = off;
@@ -107,6 +107,21 @@ struct Staged {
     }
     if (fg_h2d(dev_fallback, src, count * sizeof(T), s) != cudaSuccess) failed = true;
     return dev_fallback;
+  }
+};
+
+// Work forked onto the auxiliary stream (fg_fork) is joined back into the call's stream
+// before the call returns, also on an error path, so nothing of the call outlives it off s.
+struct AuxJoin {
+  cudaStream_t aux;
+  cudaStream_t s;
+  AuxJoin(const AuxJoin&) = delete;
+  AuxJoin& operator=(const AuxJoin&) = delete;
+  ~AuxJoin() { join(); }
+  cudaError_t join() {
+    const cudaError_t e = fg_join(aux, s);
+    aux = nullptr;
+    return e;
   }
 };
 
@@ -191,11 +206,12 @@ AssembleWork carve_assemble(const fgfrft_plan_s* p, char* base, int64_t A, int L
 }
 
 // Enqueue the fused assembly of A orders into Qc (c64 [A][N*N]) or Qs (split planes).
+// alpha_host (optional): the same orders on the host.
 cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const double* alpha_dev, int64_t A, int L,
-                         float2* Qc, __half* Qs, cudaStream_t s) {
+                         float2* Qc, __half* Qs, cudaStream_t s, const double* alpha_host = nullptr) {
   const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
   if (w.tensor) {
-    cudaError_t e = fg_coeff_planes(alpha_dev, A, L, p->L_max, p->Kp, w.Cs, w.col_exp, s);
+    cudaError_t e = fg_coeff_planes(alpha_dev, A, L, p->L_max, p->Kp, w.Cs, w.col_exp, s, alpha_host);
     if (e != cudaSuccess) return e;
     TcAssembleArgs ta{};
     ta.entry_stack = p->f16T;
@@ -210,7 +226,7 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
     ta.Qs = Qs;
     ta.N = p->N;
     ta.Np = p->Np;
-    ta.plane_elems = p->plane_elems;
+    ta.plane_elems = p->qplane;
     ta.scratch = w.scratch;
     ta.scratch_bytes = w.scratch_bytes;
     ta.status = p->dstatus;
@@ -225,7 +241,7 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
     for (int64_t a = 0; a < A; ++a) {
       e = fg_assemble_half(p->h32, p->hplane, p->nt, p->L_max, L, !p->real, p->r_neg1 > 0, p->N, p->Np,
                            w.coef + a * (2 * L + 2), Qc ? Qc + a * p->N * p->N : nullptr,
-                           Qs ? Qs + a * 4 * p->plane_elems : nullptr, p->plane_elems,
+                           Qs ? Qs + a * 4 * p->qplane : nullptr, p->qplane,
                            !(p->real && p->r_neg1 == 0), p->dstatus, s);
       if (e != cudaSuccess) return e;
     }
@@ -235,11 +251,11 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
   if (e != cudaSuccess) return e;
   if (A == 1 && p->real && p->f16)  // one order, real F: stream the two real split planes
     return fg_assemble_single_real(p->f16, 4 * p->plane_elems, p->plane_elems, b0, nb, pb, p->N, p->Np, w.coef, Qc,
-                                   Qs, p->plane_elems, p->r_neg1 > 0, p->dstatus, s);
+                                   Qs, p->qplane, p->r_neg1 > 0, p->dstatus, s);
   if (A == 1)  // one order: the bulk-copy streaming kernel, c64 or split output
     return fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, w.coef, Qc, p->dstatus, s, Qs, p->N,
-                              p->Np, p->plane_elems);
-  return fg_assemble_multi(p->c64, p->blk_elems, b0, nb, pb, p->N, (int)A, w.coef, Qc, Qs, p->Np, p->plane_elems,
+                              p->Np, p->qplane);
+  return fg_assemble_multi(p->c64, p->blk_elems, b0, nb, pb, p->N, (int)A, w.coef, Qc, Qs, p->Np, p->qplane,
                            p->dstatus, s);
 }
 
@@ -248,26 +264,26 @@ cudaError_t assemble_one(const fgfrft_plan_s* p, const float2* coef, int L, floa
   const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
   if (p->h32)
     return fg_assemble_half(p->h32, p->hplane, p->nt, p->L_max, L, !p->real, p->r_neg1 > 0, p->N, p->Np, coef, Qc, Qs,
-                            p->plane_elems, !(p->real && p->r_neg1 == 0), p->dstatus, s);
+                            p->qplane, !(p->real && p->r_neg1 == 0), p->dstatus, s);
   if (p->real && p->f16)
     return fg_assemble_single_real(p->f16, 4 * p->plane_elems, p->plane_elems, b0, nb, pb, p->N, p->Np, coef, Qc, Qs,
-                                   p->plane_elems, p->r_neg1 > 0, p->dstatus, s);
+                                   p->qplane, p->r_neg1 > 0, p->dstatus, s);
   if (p->c64)
     return fg_assemble_single(p->c64, p->blk_elems, b0, nb, pb, p->N * p->N, coef, Qc, p->dstatus, s, Qs, p->N, p->Np,
-                              p->plane_elems);
+                              p->qplane);
   return cudaErrorInvalidValue;
 }
 
 // Q_a and dQ_a/dalpha = sum_l c_l'(a) M_l + j pi e^{j pi a} P (Prop. 3) for A orders, each on
-// the single-order kernels; split outputs Qs, dQs ([A][4][plane_elems]).
+// the single-order kernels; split outputs Qs, dQs ([A][4][qplane]).
 cudaError_t run_assemble_dual(const fgfrft_plan_s* p, const AssembleWork& w, const double* alpha_dev, int64_t A,
                               int L, __half* Qs, __half* dQs, cudaStream_t s) {
   cudaError_t e = fg_coeffs(alpha_dev, (int)A, L, false, w.coef, w.coefd, 1, 2 * L + 2, s);
   if (e != cudaSuccess) return e;
   for (int64_t a = 0; a < A; ++a) {
-    e = assemble_one(p, w.coef + a * (2 * L + 2), L, nullptr, Qs + a * 4 * p->plane_elems, s);
+    e = assemble_one(p, w.coef + a * (2 * L + 2), L, nullptr, Qs + a * 4 * p->qplane, s);
     if (e != cudaSuccess) return e;
-    e = assemble_one(p, w.coefd + a * (2 * L + 2), L, nullptr, dQs + a * 4 * p->plane_elems, s);
+    e = assemble_one(p, w.coefd + a * (2 * L + 2), L, nullptr, dQs + a * 4 * p->qplane, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -321,8 +337,8 @@ ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int 
       w.group_alpha_dev = c.take<double>((size_t)groups);
       w.asm_work = carve_assemble(p, nullptr, groups, L, dual);
       w.asm_base = c.take<char>(w.asm_work.bytes);
-      w.Qs = c.take<__half>((size_t)groups * 4 * p->plane_elems);
-      if (dual) w.dQs = c.take<__half>((size_t)groups * 4 * p->plane_elems);
+      w.Qs = c.take<__half>((size_t)groups * 4 * p->qplane);
+      if (dual) w.dQs = c.take<__half>((size_t)groups * 4 * p->qplane);
       w.xs_rows = fg_tc_signal_rows(B, groups);
       w.Xs = c.take<__half>((size_t)4 * w.xs_rows * p->Np);
       w.col_exp = c.take<int>((size_t)w.xs_rows);
@@ -408,6 +424,9 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   p->blk_elems = lay.blk_elems;
   p->Np = lay.Np;
   p->plane_elems = lay.plane_elems;
+  // plane stride of the assembled split operators (work buffers); a 256-byte skew between
+  // planes measured no faster with the chunk-major entry copy, so it equals the stack's
+  p->qplane = lay.plane_elems;
   p->bytes = need;
   char* pm = (char*)plan_mem;
   p->dstatus = (uint32_t*)pm;
@@ -627,7 +646,7 @@ int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, v
   Staged st(s);
   const double* ad = st.put(a.data(), (size_t)A, w.alpha_dev);
   if (st.failed) return FGFRFT_ERR_CUDA;
-  CK(run_assemble(p, w, ad, A, L, (float2*)Q_dev, nullptr, s));
+  CK(run_assemble(p, w, ad, A, L, (float2*)Q_dev, nullptr, s, a.data()));
   return FGFRFT_OK;
 }
 
@@ -737,16 +756,23 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       const double* gad = st.put(ga.data(), ga.size(), w.group_alpha_dev);
       const int4* tiles_dev = st.put(tiles.data(), tiles.size(), (int4*)w.tc_scratch);
       if (st.failed) return FGFRFT_ERR_CUDA;
+      // the signal split runs beside the operator assembly on the auxiliary stream (they
+      // share no buffer); the GEMM waits for both
+      AuxJoin aux{fg_fork(s), s};
+      if (aux.aux)
+        CK(fg_split_signals(X, B, p->N, p->Np, w.xs_rows, w.Xs, w.col_exp, aux.aux, w.bimag, x_real));
       if (D_dev)
         CK(run_assemble_dual(p, w.asm_work, gad, groups, L, w.Qs, w.dQs, s));
       else
-        CK(run_assemble(p, w.asm_work, gad, groups, L, nullptr, w.Qs, s));
+        CK(run_assemble(p, w.asm_work, gad, groups, L, nullptr, w.Qs, s, ga.data()));
+      const bool split_done = aux.aux != nullptr;
+      CK(aux.join());
       TcGroupedArgs ta{};
       ta.tiles_dev = tiles_dev;
       ta.ntiles = (int64_t)tiles.size();
       ta.N = p->N;
       ta.Np = p->Np;
-      ta.plane_elems = p->plane_elems;
+      ta.plane_elems = p->qplane;
       ta.Qs = w.Qs;
       ta.groups = groups;
       ta.gstart = gstart.data();
@@ -764,11 +790,12 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, c
       ta.bimag = w.bimag;
       ta.x_real = x_real;
       ta.y_real = y_real;
+      ta.x_split_done = split_done;
       if (Y) CK(fg_tc_grouped_apply(ta, s));
       if (D_dev) {  // D = (dQ/dalpha) X on the same split signals
         ta.Qs = w.dQs;
         ta.Y = (float2*)D_dev;
-        ta.x_split_done = Y != nullptr;
+        ta.x_split_done = split_done || Y != nullptr;
         CK(fg_tc_grouped_apply(ta, s));
       }
       return FGFRFT_OK;

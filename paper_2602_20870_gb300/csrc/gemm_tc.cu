@@ -11,16 +11,17 @@
 //   acc_re += Ar*Xr - Ai*Xi ,  acc_im += Ar*Xi + Ai*Xr   (3 split products each term)
 // with FP32 accumulation in tensor memory (TMEM).
 //
-// CTA layout (320 threads, one CTA per SM, persistent over a tile list):
-//   warp 0      TMA producer: 3-D tensor-map loads of 4 A planes + 4 X planes per
-//               stage (32 k-values, 64-byte swizzled rows) into a 3-stage ring;
-//   warp 1      allocates 512 TMEM columns; one thread issues tcgen05.mma and
-//               tcgen05.commit; accumulators double-buffered (2 x [re 128 | im 128]);
-//   warps 2..9  epilogue (two warps per TMEM lane quadrant, alternate 32-column
-//               chunks): tcgen05.ld the finished block, undo the power-of-two
+// CTA layout (one CTA per SM, persistent over a tile list):
+//   warp 0      TMA producer: 3-D tensor-map loads of the A planes (+ the X planes unless
+//               B is resident) per stage (32 k-values, 64-byte swizzled rows) into a ring
+//               sized to the shared memory left;
+//   warp 1      allocates the TMEM columns; one thread issues tcgen05.mma and
+//               tcgen05.commit; accumulators in 2..8 buffers of [re BN | im BN];
+//   warps 2..   epilogue, groups of four warps (one per TMEM lane quadrant; 2 groups, 4 for
+//               the fused assembly): tcgen05.ld the finished block, undo the power-of-two
 //               scales, apply the per-column coefficients, and accumulate into Y/D in
 //               global memory (each output tile is owned by one CTA, blocks in order,
-//               so the sums are deterministic).
+//               so the sums are deterministic), or write the split operators.
 // Every mbarrier wait is bounded; on a timeout the CTA records it in the status word,
 // stops issuing work, waits (bounded) for its copies and MMAs in flight, frees TMEM and
 // returns.
@@ -36,9 +37,8 @@ namespace {
 constexpr int TC_BM = 128;                 // rows per tile (TMEM lanes)
 constexpr int TC_KC = 32;                  // k per stage: 32 fp16 = 64-byte rows
 constexpr int TC_PLANE_A = TC_BM * TC_KC * 2;  // 8 KB
-constexpr int TC_EPI_WARPS = 8;
-constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // producer warp, MMA warp, epilogue warps
-constexpr int TC_EPI_WARP0 = 2;
+constexpr int TC_EPI_WARP0 = 2;  // warps before the epilogue: the producer and the MMA issuer
+constexpr int TC_MAXBUF = 8;     // TMEM accumulator buffers at most
 constexpr int TC_BN_MAX = 256;
 constexpr int TC_BN_STD = 128;  // column-tile width of the stacked and complex grouped GEMMs
 
@@ -52,11 +52,26 @@ template <int BN, bool RB = false, bool RA = false>
 struct TcCfg {
   static constexpr int PLANE_B = BN * TC_KC * 2;
   static constexpr int A_PLANES = RA ? 2 : 4;
-  // 2 buffers x [re BN | im BN]; BN = 256 has 512 columns: 2 real-only buffers or 1 complex
-  static constexpr int TMEM_COLS = 4 * BN > 512 ? 512 : 4 * BN;
+  // Epilogue warps: 8, or 16 for the resident-B launch (the fused assembly), whose few MMAs
+  // per tile leave the epilogue (TMEM -> fp16 hi/lo -> global) as the critical path: four
+  // warp groups take turns on the tiles, so twice the warps hide its latencies.
+  static constexpr int EPI_WARPS = RB ? 16 : 8;
+  static constexpr int THREADS = 32 * TC_EPI_WARP0 + 32 * EPI_WARPS;
+  // accumulator columns an epilogue warp loads at a time (16 keeps 18 warps within the
+  // register file without spills)
+  static constexpr int CW = RB ? 16 : 32;
+  // 2 buffers x [re BN | im BN]; BN = 256 has 512 columns: 2 real-only buffers or 1 complex;
+  // the resident-B launch takes all 512 columns (up to 8 buffers for its four warp groups)
+  static constexpr int TMEM_COLS = RB ? 512 : (4 * BN > 512 ? 512 : 4 * BN);
   // kind::f16 instruction descriptor: D f32, A/B f16, both K-major, N = BN, M = 128.
   static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
   static constexpr uint32_t IDESC_NEG_A = IDESC | (1u << 13);
+  // N = 2 BN: the hi and lo planes of B are adjacent in shared memory (BN rows each, a
+  // whole number of 8-row swizzle atoms), so one MMA forms A*B_hi and A*B_lo side by side
+  static constexpr uint32_t IDESC_2N = (1u << 4) | ((uint32_t)(2 * BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+  // merged split products for a real product on the resident-B launch (BN = 64):
+  // acc[0:BN] = A_hi*B_hi + A_lo*B_hi, acc[BN:2BN] = A_hi*B_lo, 2 MMAs per k16 step instead of 3
+  static constexpr bool MERGE = RB && 2 * BN <= 256;
 };
 
 // Shared memory: this control block, then the resident B operand (RB: k-chunks x 4 planes),
@@ -68,8 +83,8 @@ struct __align__(1024) TcCtl {
   uint64_t full[TC_MAXST];
   uint64_t empty[TC_MAXST];
   uint64_t bfull;
-  uint64_t tfull[4];
-  uint64_t tempty[4];
+  uint64_t tfull[TC_MAXBUF];
+  uint64_t tempty[TC_MAXBUF];
   uint64_t drain;
   uint32_t tmem_base;
   volatile int abort;
@@ -99,6 +114,11 @@ struct TcParams {
   float uscale;       // nonzero: every column has this output scale (no per-column exponents)
   int y_real;         // grouped output: Y is real float32 (only the real parts are written)
   int cps;            // k-chunks per ring stage (one mbarrier handshake per group of chunks)
+  // chunk-major A (the entry-major stack): k-chunk kc < a_nfull of plane q is plane
+  // q * a_nfull + kc of the A map (32 columns each); the last chunk, narrower, is plane q
+  // of the tail map (its missing columns read as zeros)
+  int a_chunked;
+  int a_nfull;
   const int* bimag;   // NULL, or a device word that is 0 when every B column is real
   const float2* coef;
   const float2* coefd;
@@ -146,6 +166,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
       : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[32]) { tmem_ld32(taddr, v); }
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[16]) { tmem_ld16(taddr, v); }
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Bounded wait that also gives up at once when another role already aborted.
@@ -168,20 +200,20 @@ __device__ __forceinline__ int4 tile_of(const TcParams& p, int t) {
   return p.tiles ? p.tiles[t] : make_int4(t, 0, 0, p.arith_cols);
 }
 
-// Split-output epilogue of one 32-column chunk: column j0 + c of this thread's row goes to
+// Split-output epilogue of one CW-column chunk: column j0 + c of this thread's row goes to
 // Qs + (j0 + c) * 4 * qplane + qoff as fp16 hi/lo planes (re_hi, re_lo, im_hi, im_lo).
 // UNIFORM: every column has the scale p.uscale (no per-column table).
-template <bool UNIFORM>
-__device__ __forceinline__ void split_out_cols(const uint32_t (&vr)[32], const uint32_t (&vi)[32], const TcParams& p,
+template <bool UNIFORM, int CW>
+__device__ __forceinline__ void split_out_cols(const uint32_t (&vr)[CW], const uint32_t (&vi)[CW], const TcParams& p,
                                                const float* scale, int cc, int j0, int ncol, int64_t qoff) {
   const int64_t pl = p.qplane, cs = 4 * pl;
   __half* qp = p.Qs + (int64_t)j0 * cs + qoff;
   const bool write_im = !p.skip_im;
   if (!write_im) {  // real operators: the real planes only
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
+    for (int c = 0; c < CW; ++c) {
       if (c < ncol) {
-        const float re = __uint_as_float(vr[c]) * (UNIFORM ? p.uscale : scale[cc * 32 + c]);
+        const float re = __uint_as_float(vr[c]) * (UNIFORM ? p.uscale : scale[cc * CW + c]);
         const __half hi = __float2half_rn(re);
         qp[0] = hi;
         qp[pl] = __float2half_rn(re - __half2float(hi));
@@ -191,9 +223,9 @@ __device__ __forceinline__ void split_out_cols(const uint32_t (&vr)[32], const u
     return;
   }
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
+  for (int c = 0; c < CW; ++c) {
     if (c < ncol) {
-      const float sc = UNIFORM ? p.uscale : scale[cc * 32 + c];
+      const float sc = UNIFORM ? p.uscale : scale[cc * CW + c];
       const float re = __uint_as_float(vr[c]) * sc, im = __uint_as_float(vi[c]) * sc;
       const __half2 hi = __floats2half2_rn(re, im);
       const float2 hf = __half22float2(hi);
@@ -209,11 +241,15 @@ __device__ __forceinline__ void split_out_cols(const uint32_t (&vr)[32], const u
   }
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory"); }
+template <int EPI_WARPS>
+__device__ __forceinline__ void epi_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
+}
 
 template <int BN, bool RB, bool RA>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+__global__ void __launch_bounds__(TcCfg<BN, RB, RA>::THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmT, TcParams p) {
   using Cfg = TcCfg<BN, RB, RA>;
   constexpr int A_PLANES = Cfg::A_PLANES;
   constexpr int TC_BN = BN;
@@ -221,6 +257,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr int TC_TMEM_COLS = Cfg::TMEM_COLS;
   constexpr uint32_t kIdesc = Cfg::IDESC;
   constexpr uint32_t kIdescNegA = Cfg::IDESC_NEG_A;
+  constexpr int EPI_WARPS = Cfg::EPI_WARPS;
+  constexpr int NGRP = EPI_WARPS / 4;  // epilogue warp groups (each covers the 128 TMEM lanes)
+  constexpr int CW = Cfg::CW;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* const sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcCtl& sm = *reinterpret_cast<TcCtl*>(sbase);
@@ -241,22 +280,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int nst = min(TC_MAXST, (p.smem_bytes - (int)sizeof(TcCtl) - res_bytes) / stage_bytes);
   // TMEM columns of one accumulator buffer, and how many buffers fit (2: the epilogue of one
   // block overlaps the MMAs of the next)
-  const uint32_t acc_w = (re_only ? 1u : 2u) * (uint32_t)BN;
+  const bool merged = Cfg::MERGE && re_only;
+  const uint32_t acc_w = (re_only && !merged ? 1u : 2u) * (uint32_t)BN;
   // ping-pong epilogue (one block per tile and one output scale, as in the fused assembly):
-  // the two epilogue warp groups take alternate tiles, with up to four accumulator buffers
-  // so the MMAs run ahead of both
-  const bool pingpong = p.nblk == 1 && p.uscale != 0.f;
+  // the epilogue warp groups take turns on the tiles, with up to 2 buffers per group so the
+  // MMAs run ahead of all of them
   const int nbuf_fit = (int)((uint32_t)Cfg::TMEM_COLS / acc_w);
-  const int nbuf = pingpong ? min(4, nbuf_fit) : (nbuf_fit >= 2 ? 2 : 1);
+  const bool pingpong = p.nblk == 1 && p.uscale != 0.f && nbuf_fit >= NGRP;
+  const int nbuf = pingpong ? min(2 * NGRP, nbuf_fit) / NGRP * NGRP : (nbuf_fit >= 2 ? 2 : 1);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; ++s) {
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], 1);
     }
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < TC_MAXBUF; ++b) {
       mbar_init(&sm.tfull[b], 1);
-      mbar_init(&sm.tempty[b], pingpong ? TC_EPI_WARPS / 2 : TC_EPI_WARPS);
+      mbar_init(&sm.tempty[b], pingpong ? 4 : EPI_WARPS);
     }
     mbar_init(&sm.drain, 1);
     mbar_init(&sm.bfull, 1);
@@ -264,6 +304,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     fence_barrier_init();
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    if (p.a_chunked)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmT)) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
@@ -314,9 +356,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int c = 0; c < nc; ++c) {
               uint8_t* st = stages + s * stage_bytes + c * chunk_bytes;
               const int k0 = (kc0 + c) * TC_KC;
+              if (p.a_chunked) {  // chunk-major A: full 32-column chunk planes, then the tail
+                const int kc = kc0 + c;
 #pragma unroll
-              for (int q = 0; q < A_PLANES; ++q)
-                tma_load_3d(st + q * TC_PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
+                for (int q = 0; q < A_PLANES; ++q) {
+                  if (kc < p.a_nfull)
+                    tma_load_3d(st + q * TC_PLANE_A, &tmA, 0, tile.x * TC_BM, q * p.a_nfull + kc, &sm.full[s]);
+                  else
+                    tma_load_3d(st + q * TC_PLANE_A, &tmT, 0, tile.x * TC_BM, q, &sm.full[s]);
+                }
+              } else {
+#pragma unroll
+                for (int q = 0; q < A_PLANES; ++q)
+                  tma_load_3d(st + q * TC_PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
+              }
               if (!RB) {
                 for (int q = 0; q < nbp; ++q)
                   tma_load_3d(st + A_PLANES * TC_PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
@@ -382,6 +435,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               const uint64_t bih = desc_sw64(sb + 2 * TC_PLANE_B + off), bil = desc_sw64(sb + 3 * TC_PLANE_B + off);
               if (p.kvalid > 0 && kc * TC_KC + kk * 16 >= p.kvalid) continue;  // all-zero k16 step
               const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+              if (merged) {  // [A_hi*B_hi | A_hi*B_lo], then A_lo*B_hi into the first half
+                umma(d_re, arh, brh, Cfg::IDESC_2N, acc);
+                umma(d_re, arl, brh, kIdesc, 1);
+                continue;
+              }
               // real part: Ar*Xr - Ai*Xi
               umma(d_re, arh, brh, kIdesc, acc);
               umma(d_re, arh, brl, kIdesc, 1);
@@ -425,12 +483,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    // 8 warps: warps w and w+4 read the same TMEM lane quadrant (w mod 4) and take
-    // alternate 32-column chunks of the tile.
+    // NGRP groups of 4 warps; the warps of a group read the four TMEM lane quadrants
+    // (warp w may access quadrant w mod 4).  Ping-pong: group g takes the tiles li = g mod
+    // NGRP whole; otherwise the groups take alternate 32-column chunks of every tile.
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
-    const int half = (warp - TC_EPI_WARP0) >> 2;
+    const int grp = (warp - TC_EPI_WARP0) >> 2;
     const int row = 32 * q + lane;
-    const int et = threadIdx.x - TC_EPI_WARP0 * 32;  // 0..255
+    const int et = threadIdx.x - TC_EPI_WARP0 * 32;  // 0 .. 32 * EPI_WARPS - 1
     const bool split_out = p.Qs != nullptr;
     uint32_t bc = 0;
     bool ok = true;
@@ -444,9 +503,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     };
     int4 next = blockIdx.x < p.ntiles ? tile_of(p, blockIdx.x) : make_int4(0, 0, 0, 0);
     float next_scale = blockIdx.x < p.ntiles ? col_scale(next) : 0.f;
-    int64_t li = 0;  // local tile index (ping-pong: group `half` takes the tiles li = half mod 2)
+    int64_t li = 0;  // local tile index (ping-pong: group grp takes the tiles li = grp mod NGRP)
     for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++li) {
-      const bool mine = !pingpong || (int)(li & 1) == half;
+      const bool mine = !pingpong || (int)(li % NGRP) == grp;
       const int4 tile = next;
       const float my_scale = next_scale;
       if (t + (int)gridDim.x < p.ntiles) {
@@ -454,9 +513,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         next_scale = col_scale(next);
       }
       if (p.uscale == 0.f) {  // per-column scales: publish this tile's table
-        epi_bar();
+        epi_bar<EPI_WARPS>();
         if (et < TC_BN) sm.scale[et] = my_scale;
-        epi_bar();
+        epi_bar<EPI_WARPS>();
       }
       const int64_t gi = (int64_t)tile.x * TC_BM + row;
       const bool row_ok = gi < p.rows;
@@ -476,42 +535,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         fence_tc_after();
         const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + buf * acc_w;
 #pragma unroll 1
-        for (int cc = pingpong ? 0 : half; cc < TC_BN / 32; cc += pingpong ? 1 : 2) {
-          const int j0 = tile.z + cc * 32;
+        for (int cc = pingpong ? 0 : grp; cc < TC_BN / CW; cc += pingpong ? 1 : NGRP) {
+          const int j0 = tile.z + cc * CW;
           if (j0 >= tile.w) break;  // uniform: no column of this chunk is in range
-          const int ncol = min(32, tile.w - j0);
-          uint32_t vr[32], vi[32];
+          const int ncol = min(CW, tile.w - j0);
+          uint32_t vr[CW], vi[CW];
           __syncwarp();  // tcgen05.ld is warp-collective: the whole warp converged
-          tmem_ld32(base + cc * 32, vr);
-          if (re_only) {  // the imaginary accumulator was not formed: the product is real
+          tmem_ld(base + cc * CW, vr);
+          if (re_only && !merged) {  // the imaginary accumulator was not formed: the product is real
 #pragma unroll
-            for (int c = 0; c < 32; ++c) vi[c] = 0u;
+            for (int c = 0; c < CW; ++c) vi[c] = 0u;
           } else {
-            tmem_ld32(base + TC_BN + cc * 32, vi);
+            tmem_ld(base + TC_BN + cc * CW, vi);
           }
           tmem_wait_ld();
+          if (merged) {  // real product: the two halves of the merged split products
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+              vr[c] = __float_as_uint(__uint_as_float(vr[c]) + __uint_as_float(vi[c]));
+              vi[c] = 0u;
+            }
+          }
           if (!row_ok) {
             // rows past the end: nothing to store
           } else if (split_out) {
             // value * 2^FG_SPLIT_SHIFT as fp16 hi + lo, four planes per column
             if (p.uscale != 0.f)
-              split_out_cols<true>(vr, vi, p, sm.scale, cc, j0, ncol, qoff);
+              split_out_cols<true, CW>(vr, vi, p, sm.scale, cc, j0, ncol, qoff);
             else
-              split_out_cols<false>(vr, vi, p, sm.scale, cc, j0, ncol, qoff);
+              split_out_cols<false, CW>(vr, vi, p, sm.scale, cc, j0, ncol, qoff);
           } else if (p.coef == nullptr && p.y_real) {
             float* yp = reinterpret_cast<float*>(p.Y) + (int64_t)j0 * p.rows + gi;
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-              if (c < ncol) *yp = __uint_as_float(vr[c]) * sm.scale[cc * 32 + c];
+            for (int c = 0; c < CW; ++c) {
+              if (c < ncol) *yp = __uint_as_float(vr[c]) * sm.scale[cc * CW + c];
               yp += p.rows;
             }
           } else if (p.coef == nullptr) {
             float2* yp = p.Y + (int64_t)j0 * p.rows + gi;
             const bool uni = p.uscale != 0.f;
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
+            for (int c = 0; c < CW; ++c) {
               if (c < ncol) {
-                const float sc = uni ? p.uscale : sm.scale[cc * 32 + c];
+                const float sc = uni ? p.uscale : sm.scale[cc * CW + c];
                 *yp = make_float2(__uint_as_float(vr[c]) * sc, __uint_as_float(vi[c]) * sc);
               }
               yp += p.rows;
@@ -522,9 +588,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float2* cfp = p.coef + (int64_t)b * p.ldcoef + j0;
             const float2* cdp = p.D ? p.coefd + (int64_t)b * p.ldcoef + j0 : nullptr;
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
+            for (int c = 0; c < CW; ++c) {
               if (c < ncol) {
-                const float sc = sm.scale[cc * 32 + c];
+                const float sc = sm.scale[cc * CW + c];
                 const float tr = __uint_as_float(vr[c]) * sc, ti = __uint_as_float(vi[c]) * sc;
                 const float2 cf = __ldg(cfp + c);
                 float2 y = b == 0 ? make_float2(0.f, 0.f) : *yp;
@@ -631,8 +697,8 @@ int sm_count() {
 }
 
 template <int BN, bool RB, bool RA>
-cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, int ntiles, const TcParams& p, cudaStream_t s,
-                      int kclass) {
+cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mT, int ntiles,
+                      const TcParams& p, cudaStream_t s, int kclass) {
   // all the shared memory a CTA may have (one CTA per SM); the kernel sizes its ring to it
   const int smem = smem_optin();
   using Cfg = TcCfg<BN, RB, RA>;
@@ -641,12 +707,20 @@ cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, int ntiles, 
   TcParams q = p;
   q.smem_bytes = smem - 1024;  // the kernel aligns its base up to 1024 bytes
   if (q.smem_bytes - (int)sizeof(TcCtl) - res_bytes < TC_MIN_STAGES * worst_stage) return cudaErrorInvalidValue;
+  int smem_req = smem;
+  if (RB) {
+    // resident B: a stage holds A only, so the ring depth is known here; ask for just that
+    // much, leaving the rest of the SM's shared memory to kernels running beside this one
+    const int nst = std::min(TC_MAXST, (q.smem_bytes - (int)sizeof(TcCtl) - res_bytes) / worst_stage);
+    q.smem_bytes = (int)sizeof(TcCtl) + res_bytes + nst * worst_stage;
+    smem_req = q.smem_bytes + 1024;
+  }
   cudaError_t e =
-      cudaFuncSetAttribute(tc_gemm_kernel<BN, RB, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      cudaFuncSetAttribute(tc_gemm_kernel<BN, RB, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_req);
   if (e != cudaSuccess) return e;
   const int grid = std::min<int>(ntiles, sm_count());
   FgTimed timed(kclass, s);
-  tc_gemm_kernel<BN, RB, RA><<<grid, TC_THREADS, smem, s>>>(mA, mB, q);
+  tc_gemm_kernel<BN, RB, RA><<<grid, Cfg::THREADS, smem_req, s>>>(mA, mB, mT, q);
   fg_note_launch(kclass);
   return cudaGetLastError();
 }
@@ -655,7 +729,9 @@ cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, int ntiles, 
 // resident_b: every tile has the same columns (needs bn == 64 and kchunks <= TC_RB_MAXCH).
 cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vector<int4>& tiles, TcParams p,
                    void* scratch, size_t scratch_bytes, cudaStream_t s, int kclass = FGFRFT_KC_TC_GEMM,
-                   int bn = 128, bool resident_b = false, bool real_a = false) {
+                   int bn = 128, bool resident_b = false, bool real_a = false, const CUtensorMap* mTail = nullptr) {
+  const CUtensorMap& mT = mTail ? *mTail : mA;  // the tail map is read only with p.a_chunked
+  if (p.a_chunked && !mTail) return cudaErrorInvalidValue;
   if (tiles.empty()) {
     // a table already on the device (p.tiles), or arithmetic tiles (p.tiles == NULL)
     if (p.ntiles <= 0 || (!p.tiles && p.arith_cols <= 0)) return cudaSuccess;
@@ -669,18 +745,18 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vect
   }
   if (resident_b) {
     if (bn != 64 || p.kchunks > TC_RB_MAXCH) return cudaErrorInvalidValue;
-    return real_a ? launch_bn<64, true, true>(mA, mB, p.ntiles, p, s, kclass)
-                  : launch_bn<64, true, false>(mA, mB, p.ntiles, p, s, kclass);
+    return real_a ? launch_bn<64, true, true>(mA, mB, mT, p.ntiles, p, s, kclass)
+                  : launch_bn<64, true, false>(mA, mB, mT, p.ntiles, p, s, kclass);
   }
   if (bn == 256) {  // real A only (a complex A at BN = 256 leaves too few stages)
     if (!real_a) return cudaErrorInvalidValue;
-    return launch_bn<256, false, true>(mA, mB, p.ntiles, p, s, kclass);
+    return launch_bn<256, false, true>(mA, mB, mT, p.ntiles, p, s, kclass);
   }
   if (bn == 64)
-    return real_a ? launch_bn<64, false, true>(mA, mB, p.ntiles, p, s, kclass)
-                  : launch_bn<64, false, false>(mA, mB, p.ntiles, p, s, kclass);
-  return real_a ? launch_bn<128, false, true>(mA, mB, p.ntiles, p, s, kclass)
-                : launch_bn<128, false, false>(mA, mB, p.ntiles, p, s, kclass);
+    return real_a ? launch_bn<64, false, true>(mA, mB, mT, p.ntiles, p, s, kclass)
+                  : launch_bn<64, false, false>(mA, mB, mT, p.ntiles, p, s, kclass);
+  return real_a ? launch_bn<128, false, true>(mA, mB, mT, p.ntiles, p, s, kclass)
+                : launch_bn<128, false, false>(mA, mB, mT, p.ntiles, p, s, kclass);
 }
 
 }  // namespace
@@ -791,10 +867,21 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   // "signals" are their coefficient vectors over the stored blocks.
   if (a.entries > ((int64_t)1 << 37) || a.A > (1 << 20)) return cudaErrorInvalidValue;
   const int bn = a.A <= 64 ? 64 : 128;
-  CUtensorMap mA, mB;
-  if (!make_map(&mA, a.entry_stack, a.K, a.entries, a.Kp, 4, a.planeT, TC_BM) ||
+  // the entry-major stack is chunk-major: per plane, Kp / 32 full chunk planes of 32
+  // columns (64-byte rows: a TMA box is 8 KB of contiguous, aligned memory), then a
+  // tail plane of Kp mod 32 columns
+  const int64_t nfull = a.Kp / TC_KC, wtail = a.Kp % TC_KC;
+  if (a.Kp % 8 || a.Kp < a.K) return cudaErrorInvalidValue;
+  CUtensorMap mA, mB, mT;
+  const __half* tail = a.entry_stack + 4 * nfull * a.planeT * TC_KC;
+  if ((nfull > 0 && !fg_make_map_f16(&mA, a.entry_stack, TC_KC, a.entries, TC_KC, 4 * nfull, a.planeT * TC_KC,
+                                      TC_KC, TC_BM, 64)) ||
+      (wtail > 0 &&
+       !fg_make_map_f16(&mT, tail, wtail, a.entries, wtail, 4, a.planeT * wtail, TC_KC, TC_BM, 64)) ||
       !make_map(&mB, a.Cs, a.K, a.A, a.Kp, 4, a.A * a.Kp, bn))
     return cudaErrorInvalidValue;
+  if (nfull == 0) mA = mT;
+  if (wtail == 0) mT = mA;
   std::vector<int4> tiles;
   const int64_t row_tiles = (a.entries + TC_BM - 1) / TC_BM;
   if (row_tiles > INT32_MAX) return cudaErrorInvalidValue;
@@ -812,6 +899,8 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   p.rows = a.entries;
   p.kchunks = (int)((a.K + TC_KC - 1) / TC_KC);
   p.kvalid = (int)a.K;
+  p.a_chunked = 1;
+  p.a_nfull = (int)nfull;
   p.Y = a.Qc;
   p.Qs = a.Qs;
   p.qN = a.N;
@@ -834,7 +923,7 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
     const int avail = smem_optin() - 1024 - (int)sizeof(TcCtl) - res;
     p.cps = std::max(1, std::min(p.kchunks, avail / (2 * chunk)));
   }
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, bn, rb, a.real_a);
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, bn, rb, a.real_a, &mT);
 }
 
 size_t fg_tc_assemble_scratch_bytes(int64_t entries, int64_t A) {

@@ -19,16 +19,17 @@ struct fgfrft_plan_s {
   int64_t blk_elems;   // c64 entries per block (N*N padded to 32)
   int64_t Np;          // fp16 row pitch in elements (N rounded up to 8, 16-byte rows)
   int64_t plane_elems; // fp16 entries per plane (N * Np, padded to 128)
+  int64_t qplane;      // fp16 entries per plane of the assembled split operators (work buffers)
   size_t bytes;
   uint32_t* dstatus;   // device status word (bit set of kernel error codes)
   float2* c64;         // [nblk][blk_elems] or NULL
   __half* f16;         // [nblk][4][plane_elems] or NULL; planes re_hi, re_lo, im_hi, im_lo
-  __half* f16T;        // entry-major copy [4][N*N][Kp] or NULL (fused multi-order assembly)
+  __half* f16T;        // entry-major copy (chunk-major, see fg_entry_major) or NULL
   float* h32;          // half stack [L_max + 2][re, im][hplane]: M_0 .. M_L_max, then P; or NULL
   int nt;              // 64 x 64 tiles per dimension of the half stack
   int64_t hplane;      // floats per half-stack plane (nt * nt * 4096)
   int64_t Kp;          // entry-major row pitch (nblk rounded up to 8)
-  int64_t planeT;      // entries per entry-major plane (padded to 128)
+  int64_t planeT;      // entries per chunk plane of the entry-major copy (N * N padded to 128)
   int r_neg1;
   double proj_residual;
   int squarings;
@@ -181,6 +182,11 @@ cudaError_t fg_h2d(void* dst, const void* src, size_t bytes, cudaStream_t s);
 // fg_stage_done(token, s) must follow once every kernel that reads it is enqueued on s.
 int fg_stage(const void* src, size_t bytes, const void** dev);
 void fg_stage_done(int token, cudaStream_t s);
+// An auxiliary stream of the current device for work of a call that may run beside the
+// rest of it: fg_fork makes it wait for everything queued on s so far and returns it
+// (nullptr: run everything on s); fg_join makes s wait for everything queued on it so far.
+cudaStream_t fg_fork(cudaStream_t s);
+cudaError_t fg_join(cudaStream_t aux, cudaStream_t s);
 struct FgTimed {  // records a CUDA event pair around its scope when timing is enabled
   FgTimed(int cls, cudaStream_t s);
   ~FgTimed();
@@ -207,6 +213,11 @@ cudaError_t fg_ztrace_fro(int64_t N, const double2* S, const double2* Sub, doubl
 cudaError_t fg_zimag_sq(int64_t N, const double2* F, double* out, cudaStream_t s);  // out[0] = sum Im(F)^2
 cudaError_t fg_store_block(int64_t N, const double2* M, bool conj_transpose, float2* c64, __half* f16,
                            int64_t Np, int64_t plane_elems, cudaStream_t s);
+// Entry-major copy of the split stack for the fused multi-order assembly: for plane p,
+// entry e = i * N + k and stored block b < Kp (blocks nblk..Kp-1 zero), chunk-major so that
+// every 32-block chunk of 128 entries is one contiguous 8 KB tile:
+//   b < 32 * (Kp / 32):  T[((p * (Kp / 32) + b / 32) * planeT + e) * 32 + b % 32]
+//   else (the tail):     T[4 * (Kp / 32) * planeT * 32 + (p * planeT + e) * (Kp % 32) + b % 32]
 cudaError_t fg_entry_major(const __half* f16, int nblk, int64_t N, int64_t Np, int64_t plane_elems, __half* T,
                            int64_t Kp, int64_t planeT, cudaStream_t s);
 // One half-stack block (FP32 re/im planes of 64 x 64 swizzled tiles) from an FP64 matrix.
@@ -271,6 +282,8 @@ cudaError_t fg_split_signals(const void* X, int64_t B, int64_t N, int64_t Np, in
                              int* col_exp, cudaStream_t s, int* bimag = nullptr, bool x_real = false);
 // Split coefficient planes [4][A][Kp] (and per-order exponents) of the fused multi-order
 // assembly: order a's column holds c_l(alpha_a) at stored position L_max + l for |l| <= L,
-// e^{j pi alpha_a} at the P position 2 L_max + 1, zeros elsewhere.
+// e^{j pi alpha_a} at the P position 2 L_max + 1, zeros elsewhere.  alpha: the orders on the
+// device; alpha_host (optional, the same values): with at most 64 orders they travel in the
+// launch's parameters, so the kernel does not wait on a read of the table.
 cudaError_t fg_coeff_planes(const double* alpha, int64_t A, int L, int L_max, int64_t Kp, __half* planes,
-                            int* col_exp, cudaStream_t s);
+                            int* col_exp, cudaStream_t s, const double* alpha_host = nullptr);

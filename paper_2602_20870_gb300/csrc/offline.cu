@@ -236,10 +236,10 @@ __global__ void __launch_bounds__(256) store_half_kernel(int64_t N, const double
   }
 }
 
-// Entry-major copy of the split stack: T[p][e][b] = F16[b][p][e / N][e % N] for the
-// stored blocks b < nblk (e = i * N + k).  32 entries x 32 blocks per tile, staged in
-// shared memory so both the reads (along entries) and the writes (along blocks) are
-// contiguous.
+// Entry-major copy of the split stack: entry e = i * N + k of block b < nblk of plane p
+// is F16[b][p][e / N][e % N], stored at the chunk-major position fg_entry_major describes.
+// 32 entries x 32 blocks per tile, staged in shared memory so both the reads (along
+// entries) and the writes (along blocks) are contiguous.
 __global__ void __launch_bounds__(256) entry_major_kernel(const __half* __restrict__ f16, int nblk, int64_t N,
                                                           int64_t Np, int64_t plane_elems, __half* __restrict__ T,
                                                           int64_t Kp, int64_t planeT) {
@@ -263,7 +263,13 @@ __global__ void __launch_bounds__(256) entry_major_kernel(const __half* __restri
   for (int r = ty; r < 32; r += 8) {  // r: entry offset, tx: block offset
     const int64_t e = e0 + r;
     const int b = b0 + tx;
-    if (e < NN && b < Kp) T[(int64_t)p * planeT + e * Kp + b] = tile[tx][r];
+    if (e < NN && b < Kp) {
+      const int64_t nfull = Kp / 32, wtail = Kp % 32;
+      const int64_t c = b / 32;
+      const int64_t at = c < nfull ? ((p * nfull + c) * planeT + e) * 32 + (b & 31)
+                                   : 4 * nfull * planeT * 32 + (p * planeT + e) * wtail + (b & 31);
+      T[at] = tile[tx][r];
+    }
   }
 }
 

@@ -129,31 +129,43 @@ __device__ __forceinline__ float block_max256(float m, float* red) {
 // column a holds, at stored-block position q, c_l(alpha_a) for q = L_max + l with
 // |l| <= L, e^{j pi alpha_a} at q = 2 L_max + 1 (P) and zero elsewhere (q < Kp).  Every
 // coefficient has modulus at most 1, so all columns share the exponent FG_COEF_EXP
-// (values at most 2^14 in fp16).
-__global__ void __launch_bounds__(256) coeff_planes_kernel(const double* __restrict__ alpha, int L, int L_max,
-                                                           int64_t A, int64_t Kp, __half* __restrict__ planes,
-                                                           int* __restrict__ col_exp) {
+// (values at most 2^14 in fp16).  FP64 is a slow pipe on this part, so it only reduces
+// the order exactly, a = n0 + d with n0 = rint(a), |d| <= 1/2, and forms n0 - l; then in FP32
+//   sin(pi a) = (-1)^n0 sinpi(d),  cos(pi a) = (-1)^n0 cospi(d),
+//   c_l = (-1)^l sin(pi a) / (pi (d + (n0 - l)))   (c_l = 1 at a = l),
+// within a few ulp of FP32, below the 22-bit resolution of the hi/lo split it feeds.
+constexpr int COEF_PARAM_ORDERS = 64;
+struct CoefOrders {  // orders passed by value in the launch parameters
+  double a[COEF_PARAM_ORDERS];
+};
+__global__ void __launch_bounds__(256) coeff_planes_kernel(const double* __restrict__ alpha, const CoefOrders orders,
+                                                           int L, int L_max, int64_t A, int64_t Kp,
+                                                           __half* __restrict__ planes, int* __restrict__ col_exp) {
   const int64_t a_idx = blockIdx.x;
-  __shared__ double s_sc[2];
-  if (threadIdx.x == 0) {  // once per order: FP64 is a slow pipe on this part
-    s_sc[0] = sinpi(alpha[a_idx]);
-    s_sc[1] = cospi(alpha[a_idx]);
-    col_exp[a_idx] = FG_COEF_EXP;
-  }
-  __syncthreads();
-  const double a = alpha[a_idx];
-  const double sa = s_sc[0], ca = s_sc[1];
+  const double a = alpha ? alpha[a_idx] : orders.a[a_idx];
+  const double n0d = rint(a);
+  const float d = (float)(a - n0d);  // exact difference, rounded once
+  const float sgn0 = fmod(n0d, 2.0) != 0.0 ? -1.f : 1.f;
+  const float sa = sgn0 * sinpif(d), ca = sgn0 * cospif(d);
+  const float pi_f = 3.14159265358979323846f;
+  if (threadIdx.x == 0) col_exp[a_idx] = FG_COEF_EXP;
   __half* r_hi = planes + a_idx * Kp;
   for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < Kp; k0 += 4 * (int64_t)blockDim.x) {
     float2 v[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t q = k0 + u;
-      float2 c = make_float2(0.f, 0.f), cd;
-      if (q == 2 * L_max + 1)
-        block_coef(a, sa, ca, 0, true, c, cd);
-      else if (q <= 2 * L_max && q >= L_max - L && q <= L_max + L)
-        block_coef(a, sa, ca, (int)(q - L_max), false, c, cd);
+      float2 c = make_float2(0.f, 0.f);
+      if (q == 2 * L_max + 1) {
+        c = make_float2(ca, sa);
+      } else if (q <= 2 * L_max && q >= L_max - L && q <= L_max + L) {
+        const int l = (int)(q - L_max);
+        const float dl = d + (float)(n0d - (double)l);  // a - l (n0 - l exact in FP64)
+        if (dl == 0.f)
+          c.x = 1.f;
+        else
+          c.x = ((l & 1) ? -sa : sa) / (pi_f * dl);
+      }
       v[u] = c;
     }
     split_store4(v, FG_COEF_EXP, r_hi, A * Kp, k0);  // Kp is a multiple of 8
@@ -272,16 +284,18 @@ __global__ void __launch_bounds__(256) split_signals_kernel(const void* __restri
   }
 }
 
-// The same split with one warp per column (Np <= 1024, 8 columns per CTA): lane l holds
-// the groups 4(l + 32g) .. +3, g < 8, so the max needs only warp shuffles and each group's
-// plane stores are 8 bytes, 256 contiguous bytes per warp instruction.
+// The same split with one warp per column (Np <= 1024, SPLIT_WARPS columns per CTA): lane l
+// holds the groups 4(l + 32g) .. +3, g < 8, so the max needs only warp shuffles and each
+// group's plane stores are 8 bytes, 256 contiguous bytes per warp instruction.  Small CTAs
+// fit beside a CTA of the operator assembly, which the split runs next to.
+constexpr int SPLIT_WARPS = 4;
 template <bool XR>
-__global__ void __launch_bounds__(256) split_signals_warp_kernel(const void* __restrict__ Xv, int64_t B, int64_t N,
+__global__ void __launch_bounds__(32 * SPLIT_WARPS) split_signals_warp_kernel(const void* __restrict__ Xv, int64_t B, int64_t N,
                                                                  int64_t Np, int64_t rows_pad,
                                                                  __half* __restrict__ planes,
                                                                  int* __restrict__ col_exp, int* __restrict__ bimag) {
   const int lane = threadIdx.x & 31;
-  const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t j = (int64_t)blockIdx.x * SPLIT_WARPS + (threadIdx.x >> 5);
   if (j >= rows_pad) return;
   const int64_t plane = rows_pad * Np;
   __half* r_hi = planes + j * Np;
@@ -362,11 +376,11 @@ cudaError_t fg_split_signals(const void* X, int64_t B, int64_t N, int64_t Np, in
   const unsigned grid = (unsigned)rows_pad;
   auto go = [&](auto kern) { kern<<<grid, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag); };
   if (Np <= 1024) {  // a warp per column
-    const unsigned g8 = (unsigned)((rows_pad + 7) / 8);
+    const unsigned gw = (unsigned)((rows_pad + SPLIT_WARPS - 1) / SPLIT_WARPS);
     if (x_real)
-      split_signals_warp_kernel<true><<<g8, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
+      split_signals_warp_kernel<true><<<gw, 32 * SPLIT_WARPS, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
     else
-      split_signals_warp_kernel<false><<<g8, 256, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
+      split_signals_warp_kernel<false><<<gw, 32 * SPLIT_WARPS, 0, s>>>(X, B, N, Np, rows_pad, planes, col_exp, bimag);
     return cudaGetLastError();
   }
   if (x_real) {
@@ -382,11 +396,16 @@ cudaError_t fg_split_signals(const void* X, int64_t B, int64_t N, int64_t Np, in
 }
 
 cudaError_t fg_coeff_planes(const double* alpha, int64_t A, int L, int L_max, int64_t Kp, __half* planes,
-                            int* col_exp, cudaStream_t s) {
+                            int* col_exp, cudaStream_t s, const double* alpha_host) {
   if (A <= 0) return cudaSuccess;
   if (A > INT32_MAX || Kp < 2 * (int64_t)L_max + 2 || Kp % 8) return cudaErrorInvalidValue;
   FgTimed timed(FGFRFT_KC_COEFFS, s);
   fg_note_launch(FGFRFT_KC_COEFFS);
-  coeff_planes_kernel<<<(unsigned)A, 256, 0, s>>>(alpha, L, L_max, A, Kp, planes, col_exp);
+  CoefOrders ord{};
+  if (alpha_host && A <= COEF_PARAM_ORDERS) {
+    for (int64_t i = 0; i < A; ++i) ord.a[i] = alpha_host[i];
+    alpha = nullptr;
+  }
+  coeff_planes_kernel<<<(unsigned)A, 256, 0, s>>>(alpha, ord, L, L_max, A, Kp, planes, col_exp);
   return cudaGetLastError();
 }

@@ -1,4 +1,5 @@
-// Pinned staging of the small per-call host tables (orders, tile lists, group tables).
+// Pinned staging of the small per-call host tables (orders, tile lists, group tables), and
+// the auxiliary stream of each device (fg_fork / fg_join).
 //
 // cudaMemcpyAsync from pageable host memory returns only once the copy has been staged,
 // which waits for the stream to reach it: every call would then hold the host until the
@@ -20,6 +21,12 @@ constexpr int kSlots = 64;
 constexpr size_t kSlotBytes = 256 * 1024;
 constexpr int kMaxDevices = 64;
 
+struct Aux {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool failed = false;
+};
+
 struct Ring {
   char* base = nullptr;
   char* dbase = nullptr;  // device address of base
@@ -32,6 +39,28 @@ struct Ring {
 
 std::mutex g_mu;
 Ring g_ring[kMaxDevices];
+std::mutex g_aux_mu;
+Aux g_aux[kMaxDevices];
+
+bool aux_init(Aux& a, cudaStream_t s) {
+  if (a.stream) return true;
+  if (a.failed) return false;
+  // no stream or event is created while s is being captured into a graph
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaStreamCreateWithFlags(&a.stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    a.failed = true;
+    a.stream = nullptr;
+    return false;
+  }
+  return true;
+}
 
 bool ring_init(Ring& r) {
   if (r.base) return true;
@@ -125,4 +154,29 @@ void fg_stage_done(int token, cudaStream_t s) {
     cudaStreamSynchronize(s);
   }
   r.held[k] = false;
+}
+
+cudaStream_t fg_fork(cudaStream_t s) {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> g(g_aux_mu);
+  Aux& a = g_aux[d];
+  if (!aux_init(a, s)) return nullptr;
+  if (cudaEventRecord(a.fork, s) != cudaSuccess || cudaStreamWaitEvent(a.stream, a.fork, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.stream;
+}
+
+cudaError_t fg_join(cudaStream_t aux, cudaStream_t s) {
+  if (!aux) return cudaSuccess;
+  int d = 0;
+  cudaError_t e = cudaGetDevice(&d);
+  if (e != cudaSuccess) return e;
+  if (d < 0 || d >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_aux_mu);
+  e = cudaEventRecord(g_aux[d].join, aux);
+  if (e != cudaSuccess) return e;
+  return cudaStreamWaitEvent(s, g_aux[d].join, 0);
 }

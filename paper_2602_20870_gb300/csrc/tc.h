@@ -71,11 +71,13 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s);
 // stored blocks k (zero coefficients outside -L..L), from the entry-major split stack and
 // the split coefficient planes Cs (filled by fg_coeff_planes).
 struct TcAssembleArgs {
-  const __half* entry_stack;  // [4 planes][entries][Kp] fp16 (scaled by 2^FG_SPLIT_SHIFT)
+  // chunk-major fp16 (scaled by 2^FG_SPLIT_SHIFT): [4 planes][Kp / 32][planeT][32], then
+  // the tail [4 planes][planeT][Kp mod 32]
+  const __half* entry_stack;
   int64_t entries;            // N * N
   int64_t K;                  // stored blocks (2 L_max + 2)
-  int64_t Kp;                 // row pitch of the entry-major planes (K rounded up to 8)
-  int64_t planeT;             // entries per entry-major plane (padded)
+  int64_t Kp;                 // K rounded up to 8
+  int64_t planeT;             // entries per chunk plane (N * N padded to 128)
   int64_t A;
   const __half* Cs;           // [4][A][Kp] split coefficients
   const int* col_exp;         // [A] their exponents

@@ -53,6 +53,11 @@ def test_plan_bytes_layout(lib):
     plane = -(-(N * Np) // 128) * 128
     c64 = -(-((2 * L + 2) * (-(-(N * N) // 32) * 32) * 8) // 256) * 256
     assert f(N, L, 3) == 256 + c64 + -(-((2 * L + 2) * 4 * plane * 2) // 256) * 256
+    # entry-major copy: 4 planes x Kp (2L+2 rounded up to 8) chunk columns x N*N entries
+    # (padded to 128), 2 bytes
+    Kp = -(-(2 * L + 2) // 8) * 8
+    entry = -(-(4 * Kp * (-(-(N * N) // 128) * 128) * 2) // 256) * 256
+    assert f(N, L, 7) == 256 + c64 + -(-((2 * L + 2) * 4 * plane * 2) // 256) * 256 + entry
     # half stack: M_0..M_L and P, L + 2 blocks of two FP32 planes of 64 x 64 tiles
     nt = -(-N // 64)
     assert f(N, L, 8) == 256 + -(-((L + 2) * 2 * nt * nt * 4096 * 4) // 256) * 256
