@@ -400,7 +400,19 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA>::THREADS, 1)
       uint32_t ph_cur = 0, bc = 0;
       bool ok = true;
       if (RB && blockIdx.x < p.ntiles) ok = tc_wait(&sm.bfull, 0, sm, p.status);
+      // grouped tiles may be narrower than BN (ragged groups, halved last-wave tiles): each
+      // tile's MMAs take N = its columns rounded up to 16 (the rest of B is not read)
+      const bool tile_n = p.tiles != nullptr && p.grouped;
+      int4 next = tile_n && blockIdx.x < p.ntiles ? tile_of(p, blockIdx.x) : make_int4(0, 0, 0, 0);
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
+        uint32_t idesc = kIdesc, idesc_neg = kIdescNegA;
+        if (tile_n) {
+          const int4 tl = next;
+          if (t + (int)gridDim.x < p.ntiles) next = tile_of(p, t + gridDim.x);  // prefetch
+          const int n16 = min(TC_BN, max(16, (tl.w - tl.z + 15) / 16 * 16));
+          idesc = (kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(n16 >> 3) << 17);
+          idesc_neg = idesc | (1u << 13);
+        }
         for (int b = 0; ok && b < p.nblk; ++b, ++bc) {
           const uint32_t buf = bc % (uint32_t)nbuf, tph = (bc / (uint32_t)nbuf) & 1;
           if (!tc_wait(&sm.tempty[buf], tph ^ 1, sm, p.status)) {
@@ -437,35 +449,35 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA>::THREADS, 1)
               const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
               if (merged) {  // [A_hi*B_hi | A_hi*B_lo], then A_lo*B_hi into the first half
                 umma(d_re, arh, brh, Cfg::IDESC_2N, acc);
-                umma(d_re, arl, brh, kIdesc, 1);
+                umma(d_re, arl, brh, idesc, 1);
                 continue;
               }
               // real part: Ar*Xr - Ai*Xi
-              umma(d_re, arh, brh, kIdesc, acc);
-              umma(d_re, arh, brl, kIdesc, 1);
-              umma(d_re, arl, brh, kIdesc, 1);
+              umma(d_re, arh, brh, idesc, acc);
+              umma(d_re, arh, brl, idesc, 1);
+              umma(d_re, arl, brh, idesc, 1);
               if (re_only) continue;  // real product: no imaginary accumulator
               if (breal) {            // complex A, real X: Im = Ai*Xr only
                 if (!RA) {
                   const uint64_t aih = desc_sw64(sa + 2 * TC_PLANE_A + off), ail = desc_sw64(sa + 3 * TC_PLANE_A + off);
-                  umma(d_im, aih, brh, kIdesc, acc);
-                  umma(d_im, aih, brl, kIdesc, 1);
-                  umma(d_im, ail, brh, kIdesc, 1);
+                  umma(d_im, aih, brh, idesc, acc);
+                  umma(d_im, aih, brl, idesc, 1);
+                  umma(d_im, ail, brh, idesc, 1);
                 }
                 continue;
               }
               // imaginary part: Ar*Xi + Ai*Xr
-              umma(d_im, arh, bih, kIdesc, acc);
-              umma(d_im, arh, bil, kIdesc, 1);
-              umma(d_im, arl, bih, kIdesc, 1);
+              umma(d_im, arh, bih, idesc, acc);
+              umma(d_im, arh, bil, idesc, 1);
+              umma(d_im, arl, bih, idesc, 1);
               if (!RA) {
                 const uint64_t aih = desc_sw64(sa + 2 * TC_PLANE_A + off), ail = desc_sw64(sa + 3 * TC_PLANE_A + off);
-                umma(d_re, aih, bih, kIdescNegA, 1);
-                umma(d_re, aih, bil, kIdescNegA, 1);
-                umma(d_re, ail, bih, kIdescNegA, 1);
-                umma(d_im, aih, brh, kIdesc, 1);
-                umma(d_im, aih, brl, kIdesc, 1);
-                umma(d_im, ail, brh, kIdesc, 1);
+                umma(d_re, aih, bih, idesc_neg, 1);
+                umma(d_re, aih, bil, idesc_neg, 1);
+                umma(d_re, ail, bih, idesc_neg, 1);
+                umma(d_im, aih, brh, idesc, 1);
+                umma(d_im, aih, brl, idesc, 1);
+                umma(d_im, ail, brh, idesc, 1);
               }
             }
             }                           // chunks of the stage
@@ -793,6 +805,23 @@ void fg_tc_grouped_tiles(int64_t N, int64_t groups, const int64_t* gstart, const
     for (int rt = 0; rt < row_tiles; ++rt)
       for (int64_t c = c0; c < c1; c += bn)
         tiles.push_back(make_int4(rt, (int)(4 * g), (int)c, (int)std::min<int64_t>(c + bn, c1)));
+  }
+  // Persistent CTAs take tiles t, t + P, ...: a last wave of R <= P/2 tiles would leave most
+  // SMs idle for a whole tile, so its tiles are halved along the columns (the kernel sizes
+  // each tile's MMAs to its columns) and the wave takes half as long.
+  const int64_t P = sm_count(), T = (int64_t)tiles.size(), R = T % P;
+  if (T > P && R > 0 && 2 * R <= P) {
+    std::vector<int4> tail(tiles.end() - R, tiles.end());
+    tiles.resize((size_t)(T - R));
+    for (const int4& t : tail) {
+      const int half = ((t.w - t.z + 1) / 2 + 15) / 16 * 16;  // a multiple of 16 columns
+      if (t.w - t.z > 16 && t.z + half < t.w) {
+        tiles.push_back(make_int4(t.x, t.y, t.z, t.z + half));
+        tiles.push_back(make_int4(t.x, t.y, t.z + half, t.w));
+      } else {
+        tiles.push_back(t);
+      }
+    }
   }
 }
 
