@@ -34,6 +34,15 @@
  *     stream).  Calls enqueue work on it and return without synchronising,
  *     except fgfrft_precompute (which reads reductions back) and
  *     fgfrft_plan_status.
+ *   - fgfrft_assemble, fgfrft_apply and fgfrft_grad may be captured into a
+ *     CUDA graph (stream capture): the call's orders and host tables are then
+ *     carried by the captured kernels and written into the work buffer at
+ *     every replay, which reads the signals and writes the outputs at replay
+ *     time.  The work buffer of a graph must not be in use by another call
+ *     while the graph replays.  (The library's auxiliary stream, on which the
+ *     assembled path runs its signal split beside the operator assembly, is
+ *     created by the first uncaptured call; a capture before any such call
+ *     runs the split in line.)
  *   - Argument errors are detected on the host before anything is enqueued.
  *     CUDA launch errors return FGFRFT_ERR_CUDA.  Errors found by kernels
  *     (a bounded wait that ran out) are recorded in the plan's device status

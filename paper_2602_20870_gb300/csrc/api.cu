@@ -90,7 +90,8 @@ struct Staged {
   int tok[8];
   int n = 0;
   bool failed = false;
-  explicit Staged(cudaStream_t st) : s(st) {}
+  bool capturing;  // a graph replays later: tables go into the work buffer (fg_upload)
+  explicit Staged(cudaStream_t st) : s(st), capturing(fg_capturing(st)) {}
   Staged(const Staged&) = delete;
   Staged& operator=(const Staged&) = delete;
   ~Staged() {
@@ -100,7 +101,7 @@ struct Staged {
   template <class T>
   const T* put(const T* src, size_t count, T* dev_fallback) {
     const void* dev = nullptr;
-    const int t = n < 8 ? fg_stage(src, count * sizeof(T), &dev) : -1;
+    const int t = n < 8 && !capturing ? fg_stage(src, count * sizeof(T), &dev) : -1;
     if (t >= 0) {
       tok[n++] = t;
       return static_cast<const T*>(dev);

@@ -182,6 +182,11 @@ cudaError_t fg_h2d(void* dst, const void* src, size_t bytes, cudaStream_t s);
 // fg_stage_done(token, s) must follow once every kernel that reads it is enqueued on s.
 int fg_stage(const void* src, size_t bytes, const void** dev);
 void fg_stage_done(int token, cudaStream_t s);
+// True while s is being captured into a CUDA graph.
+bool fg_capturing(cudaStream_t s);
+// dst (device) <- src (host), bytes carried in the parameters of small kernels: what a graph
+// captures keeps the bytes (used for the host tables of a call under capture).
+cudaError_t fg_upload(void* dst, const void* src, size_t bytes, cudaStream_t s);
 // An auxiliary stream of the current device for work of a call that may run beside the
 // rest of it: fg_fork makes it wait for everything queued on s so far and returns it
 // (nullptr: run everything on s); fg_join makes s wait for everything queued on it so far.

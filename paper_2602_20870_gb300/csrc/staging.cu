@@ -1,6 +1,11 @@
 // Pinned staging of the small per-call host tables (orders, tile lists, group tables), and
 // the auxiliary stream of each device (fg_fork / fg_join).
 //
+// A stream being captured into a CUDA graph takes neither: a graph replays long after the
+// call, when the slots hold other calls' tables, so under capture the tables are written
+// into the caller's work buffer by small kernels whose parameters carry the bytes
+// (fg_upload), and the graph keeps them with its kernel nodes.
+//
 // cudaMemcpyAsync from pageable host memory returns only once the copy has been staged,
 // which waits for the stream to reach it: every call would then hold the host until the
 // device has drained the work queued before it, and the device would idle while the host
@@ -10,6 +15,7 @@
 // A slot is reused only after the work that reads it has run (one event per slot, recorded
 // by fg_stage_done or after fg_h2d's copy).  A table larger than a slot, or any table when
 // pinned memory is unavailable, takes a stream copy.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -102,10 +108,43 @@ int take_slot(Ring& r) {
   return -1;
 }
 
+constexpr int kUploadBytes = 3072;  // payload per upload kernel (kernel parameters <= 4 KB)
+struct UploadChunk {
+  unsigned char b[kUploadBytes];
+};
+__global__ void upload_kernel(unsigned char* __restrict__ dst, const UploadChunk chunk, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = chunk.b[i];
+}
+
 }  // namespace
+
+bool fg_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+cudaError_t fg_upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  const unsigned char* in = static_cast<const unsigned char*>(src);
+  unsigned char* out = static_cast<unsigned char*>(dst);
+  UploadChunk chunk;
+  for (size_t off = 0; off < bytes; off += kUploadBytes) {
+    const int n = (int)std::min<size_t>(kUploadBytes, bytes - off);
+    std::memcpy(chunk.b, in + off, (size_t)n);
+    upload_kernel<<<(n + 255) / 256, 256, 0, s>>>(out + off, chunk, n);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t fg_h2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   if (bytes == 0) return cudaSuccess;
+  if (fg_capturing(s)) return fg_upload(dst, src, bytes, s);
   int dev = 0;
   if (bytes <= kSlotBytes && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevices) {
     std::lock_guard<std::mutex> g(g_mu);

@@ -38,6 +38,7 @@ FgTimed::FgTimed(int cls, cudaStream_t s) : cls_(cls), s_(s), slot_(-1) {
   Timing& t = T();
   std::lock_guard<std::mutex> g(t.mu);
   if (!t.enabled || cls < 0 || cls >= FGFRFT_KC_COUNT) return;
+  if (fg_capturing(s)) return;  // an event pair inside a graph has no elapsed time
   ClassLog& c = t.cls[cls];
   if (c.used >= kMaxPairs) return;
   if (c.used == c.start.size()) {
