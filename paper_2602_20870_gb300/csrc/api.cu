@@ -54,23 +54,30 @@ inline bool aligned(const void* p, size_t a = kAlign) { return ((uintptr_t)p % a
     if (_e != cudaSuccess) return FGFRFT_ERR_CUDA; \
   } while (0)
 
-// Host copy of the orders, validated.  Returns FGFRFT_OK or an error code.
+// x (finite) is an integer: every double of magnitude >= 2^52 is; below, the truncation
+// to int64 is exact and compares equal only for integers.
+inline bool is_integer(double x) { return fabs(x) >= 4503599627370496.0 || x == (double)(int64_t)x; }
+
+// Host copy of the orders, validated.  Returns FGFRFT_OK or an error code.  (Runs once per
+// call over B orders: B is 16384 on the image-graph batch, so the loop is kept cheap.)
 int gather_orders(const double* alpha_host, int64_t B, int L, int flags, std::vector<double>& out) {
   if (!alpha_host || B < 1) return FGFRFT_ERR_INVALID_ARG;
   out.resize((size_t)B);
   const bool shared = (flags & FGFRFT_SHARED_ALPHA) != 0;
+  const double Ld = (double)L;
   for (int64_t j = 0; j < B; ++j) {
     const double a = shared ? alpha_host[0] : alpha_host[j];
     if (!isfinite(a)) return FGFRFT_ERR_INVALID_ARG;
-    if (a == nearbyint(a) && fabs(a) > (double)L) return FGFRFT_ERR_UNSUPPORTED;
+    if (fabs(a) > Ld && is_integer(a)) return FGFRFT_ERR_UNSUPPORTED;
     out[(size_t)j] = a;
   }
   return FGFRFT_OK;
 }
 
 // Runs of equal orders: (start, length).
-std::vector<std::pair<int64_t, int64_t>> order_runs(const std::vector<double>& a) {
-  std::vector<std::pair<int64_t, int64_t>> runs;
+using Runs = std::vector<std::pair<int64_t, int64_t>>;
+Runs order_runs(const std::vector<double>& a) {
+  Runs runs;
   int64_t s = 0;
   for (int64_t j = 1; j <= (int64_t)a.size(); ++j) {
     if (j == (int64_t)a.size() || a[(size_t)j] != a[(size_t)s]) {
@@ -140,14 +147,13 @@ struct Carve {
 
 constexpr int kAssembledMinRun = 64;
 
-int choose_path(const fgfrft_plan_s* p, const std::vector<double>& a, int flags) {
+int choose_path(const fgfrft_plan_s* p, const Runs& runs, int flags) {
   int path = flags & FGFRFT_PATH_MASK;
   if (path) return path;
   if (flags & FGFRFT_REAL_OUTPUT) return FGFRFT_PATH_ASSEMBLED;  // real outputs come from assembled Q
   const bool tensor = (p->storage & FGFRFT_STORE_SPLIT_F16) != 0 && fg_tc_available();
   if (!p->f16 && !p->c64)  // half stack only: assemble per order group, then Q X
     return fg_tc_available() ? FGFRFT_PATH_ASSEMBLED : FGFRFT_PATH_PLAIN;
-  auto runs = order_runs(a);
   int64_t min_run = INT64_MAX;
   for (auto& r : runs) min_run = std::min(min_run, r.second);
   if (min_run >= kAssembledMinRun) {
@@ -160,14 +166,14 @@ int choose_path(const fgfrft_plan_s* p, const std::vector<double>& a, int flags)
 // Path of fgfrft_grad: long runs of one order assemble Q and dQ/dalpha per run (assembled
 // path on the tensor cores, else the plain path); short runs use the stacked form.  A plan
 // with the half stack only always assembles.
-int grad_path(const fgfrft_plan_s* p, const std::vector<double>& a, int flags) {
+int grad_path(const fgfrft_plan_s* p, const Runs& runs, int flags) {
   int path = flags & FGFRFT_PATH_MASK;
   if (path) return path;
   const bool tc = fg_tc_available();
   const bool single = p->h32 || p->c64 || (p->real && p->f16);  // single-order kernels available
   if (!p->f16 && !p->c64) return tc ? FGFRFT_PATH_ASSEMBLED : FGFRFT_PATH_PLAIN;
   int64_t min_run = INT64_MAX;
-  for (auto& r : order_runs(a)) min_run = std::min(min_run, r.second);
+  for (auto& r : runs) min_run = std::min(min_run, r.second);
   if (min_run >= kAssembledMinRun && single) return tc ? FGFRFT_PATH_ASSEMBLED : FGFRFT_PATH_PLAIN;
   return (p->f16 && tc) ? FGFRFT_PATH_STACKED : FGFRFT_PATH_STACKED_FP32;
 }
@@ -621,8 +627,9 @@ size_t fgfrft_work_bytes(fgfrft_plan p, int op, const double* alpha_host, int64_
   if (gather_orders(alpha_host, count, L, flags, a) != FGFRFT_OK) return 0;
   if (flags & FGFRFT_ADJOINT)
     for (auto& v : a) v = -v;
-  const int path = op == FGFRFT_OP_GRAD ? grad_path(p, a, flags) : choose_path(p, a, flags);
-  const int64_t groups = (int64_t)order_runs(a).size();
+  const Runs runs = order_runs(a);
+  const int path = op == FGFRFT_OP_GRAD ? grad_path(p, runs, flags) : choose_path(p, runs, flags);
+  const int64_t groups = (int64_t)runs.size();
   if (op == FGFRFT_OP_GRAD) {
     // the dual forward, the backward at -alpha (the same runs) and the gradient partials
     return carve_apply(p, nullptr, count, L, path, groups, true, true).bytes;
@@ -651,13 +658,14 @@ int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, v
   return FGFRFT_OK;
 }
 
-static int apply_impl(fgfrft_plan p, std::vector<double>& a, int64_t B, int L, const void* X_dev, void* Y_dev,
-                      void* D_dev, int path, void* work, size_t work_bytes, cudaStream_t s, int real_io = 0) {
+// runs: order_runs(a) (the caller's; negating every order keeps the runs).
+static int apply_impl(fgfrft_plan p, std::vector<double>& a, const Runs& runs, int64_t B, int L, const void* X_dev,
+                      void* Y_dev, void* D_dev, int path, void* work, size_t work_bytes, cudaStream_t s,
+                      int real_io = 0) {
   const bool x_real = (real_io & FGFRFT_REAL_SIGNALS) != 0, y_real = (real_io & FGFRFT_REAL_OUTPUT) != 0;
   if ((x_real && path != FGFRFT_PATH_ASSEMBLED && path != FGFRFT_PATH_STACKED) ||
       (y_real && (!x_real || path != FGFRFT_PATH_ASSEMBLED || !p->real || p->r_neg1 != 0 || D_dev)))
     return FGFRFT_ERR_UNSUPPORTED;
-  const auto runs = order_runs(a);
   const int64_t groups = (int64_t)runs.size();
   ApplyWork w = carve_apply(p, (char*)work, B, L, path, groups, false, D_dev != nullptr);
   if (work_bytes < w.bytes) return FGFRFT_ERR_INVALID_ARG;
@@ -850,9 +858,10 @@ int fgfrft_apply(fgfrft_plan p, const double* alpha_host, int64_t B, int L, cons
   if (rc) return rc;
   if (flags & FGFRFT_ADJOINT)
     for (auto& v : a) v = -v;
-  const int path = choose_path(p, a, flags);
+  const Runs runs = order_runs(a);
+  const int path = choose_path(p, runs, flags);
   if (path == FGFRFT_PATH_PLAIN && !p->c64 && !(p->real && p->f16) && !p->h32) return FGFRFT_ERR_UNSUPPORTED;
-  return apply_impl(p, a, B, L, X_dev, Y_dev, nullptr, path, work, work_bytes, (cudaStream_t)stream, real_io);
+  return apply_impl(p, a, runs, B, L, X_dev, Y_dev, nullptr, path, work, work_bytes, (cudaStream_t)stream, real_io);
 }
 
 int fgfrft_grad(fgfrft_plan p, const double* alpha_host, int64_t B, int L, const void* X_dev, void* Y_dev,
@@ -868,13 +877,14 @@ int fgfrft_grad(fgfrft_plan p, const double* alpha_host, int64_t B, int L, const
   std::vector<double> a;
   int rc = gather_orders(alpha_host, B, L, flags & ~FGFRFT_ADJOINT, a);
   if (rc) return rc;
-  const int path = grad_path(p, a, flags);
-  const int64_t groups = (int64_t)order_runs(a).size();
+  const Runs runs = order_runs(a);
+  const int path = grad_path(p, runs, flags);
+  const int64_t groups = (int64_t)runs.size();
   ApplyWork w = carve_apply(p, (char*)work, B, L, path, groups, true, true);
   if (work_bytes < w.bytes) return FGFRFT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (X_dev) {
-    rc = apply_impl(p, a, B, L, X_dev, Y_dev, dY_dev, path, work, work_bytes, s);
+    rc = apply_impl(p, a, runs, B, L, X_dev, Y_dev, dY_dev, path, work, work_bytes, s);
     if (rc) return rc;
   }
   if (G_dev) {
@@ -882,7 +892,7 @@ int fgfrft_grad(fgfrft_plan p, const double* alpha_host, int64_t B, int L, const
     if (gradX_dev) {
       std::vector<double> na(a);
       for (auto& v : na) v = -v;
-      rc = apply_impl(p, na, B, L, G_dev, gradX_dev, nullptr, path, work, work_bytes, s);
+      rc = apply_impl(p, na, runs, B, L, G_dev, gradX_dev, nullptr, path, work, work_bytes, s);
       if (rc) return rc;
     }
   }

@@ -197,6 +197,19 @@ class Plan:
         except Exception:
             pass
 
+    def _with_work(self, op: int, alpha: np.ndarray, count: int, L: int, flags: int, call) -> int:
+        """call(w) -> status with the cached work buffer; the buffer is sized (a host pass over
+        the orders in fgfrft_work_bytes) only when there is none yet or the call reports it too
+        small, which it does before enqueuing anything."""
+        if self._work is not None:
+            rc = call(self._work)
+            if rc != ERR_INVALID_ARG:
+                return rc
+            need = _lib().fgfrft_work_bytes(self._h, op, alpha.ctypes.data_as(ctypes.c_void_p), count, L, flags)
+            if need == 0 or need <= self._work.numel():
+                return rc  # an argument error, not the buffer size
+        return call(self.work_tensor(op, alpha, count, L, flags))
+
     def work_tensor(self, op: int, alpha: np.ndarray, count: int, L: int, flags: int) -> torch.Tensor:
         n = _lib().fgfrft_work_bytes(self._h, op, alpha.ctypes.data_as(ctypes.c_void_p), count, L, flags)
         if n == 0:
@@ -248,9 +261,9 @@ class Plan:
         A = a.size
         if out is None:
             out = torch.empty((A, self.N, self.N), dtype=torch.complex64, device=self.device)
-        w = self.work_tensor(OP_ASSEMBLE, a, A, L, 0)
-        rc = _lib().fgfrft_assemble(self._h, a.ctypes.data_as(ctypes.c_void_p), A, L, _ptr(out), _ptr(w),
-                                    w.numel(), ctypes.c_void_p(_stream(stream)))
+        rc = self._with_work(OP_ASSEMBLE, a, A, L, 0, lambda w: _lib().fgfrft_assemble(
+            self._h, a.ctypes.data_as(ctypes.c_void_p), A, L, _ptr(out), _ptr(w), w.numel(),
+            ctypes.c_void_p(_stream(stream))))
         _check(rc, "fgfrft_assemble")
         return out
 
@@ -273,9 +286,9 @@ class Plan:
             (REAL_OUTPUT if real_io and real_output else 0)
         ydt = torch.float32 if (real_io and real_output) else torch.complex64
         Y = torch.empty(Xd.shape, dtype=ydt, device=self.device) if (out is None or host) else out
-        w = self.work_tensor(OP_APPLY, a, B, L, flags)
-        rc = _lib().fgfrft_apply(self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, _ptr(Xd), _ptr(Y), flags,
-                                 _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream)))
+        rc = self._with_work(OP_APPLY, a, B, L, flags, lambda w: _lib().fgfrft_apply(
+            self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, _ptr(Xd), _ptr(Y), flags, _ptr(w), w.numel(),
+            ctypes.c_void_p(_stream(stream))))
         _check(rc, "fgfrft_apply")
         if host:
             dst = out if out is not None else torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True)
@@ -292,9 +305,9 @@ class Plan:
         flags = PATHS[path]
         Y = torch.empty_like(X)
         D = torch.empty_like(X)
-        w = self.work_tensor(OP_GRAD, a, B, L, flags)
-        rc = _lib().fgfrft_grad(self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, _ptr(X), _ptr(Y), _ptr(D),
-                                None, None, None, flags, _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream)))
+        rc = self._with_work(OP_GRAD, a, B, L, flags, lambda w: _lib().fgfrft_grad(
+            self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, _ptr(X), _ptr(Y), _ptr(D), None, None, None, flags,
+            _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream))))
         _check(rc, "fgfrft_grad(forward)")
         return Y, D
 
@@ -308,10 +321,9 @@ class Plan:
         flags = PATHS[path]
         gX = torch.empty_like(G) if need_x else None
         ga = torch.empty(B, dtype=torch.float32, device=G.device) if D is not None else None
-        w = self.work_tensor(OP_GRAD, a, B, L, flags)
-        rc = _lib().fgfrft_grad(self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, None, None, _ptr(D),
-                                _ptr(G), _ptr(gX), _ptr(ga), flags, _ptr(w), w.numel(),
-                                ctypes.c_void_p(_stream(stream)))
+        rc = self._with_work(OP_GRAD, a, B, L, flags, lambda w: _lib().fgfrft_grad(
+            self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, None, None, _ptr(D), _ptr(G), _ptr(gX), _ptr(ga),
+            flags, _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream))))
         _check(rc, "fgfrft_grad(backward)")
         return gX, ga
 
