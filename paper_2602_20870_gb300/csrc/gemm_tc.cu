@@ -727,16 +727,9 @@ cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, const CUtens
     q.smem_bytes = (int)sizeof(TcCtl) + res_bytes + nst * worst_stage;
     smem_req = q.smem_bytes + 1024;
   }
-  // the attribute is set once per device and size (the call costs host time on every launch)
-  static int attr_set[64] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e =
+      cudaFuncSetAttribute(tc_gemm_kernel<BN, RB, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_req);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || attr_set[dev] != smem_req) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<BN, RB, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_req);
-    if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) attr_set[dev] = smem_req;
-  }
   const int grid = std::min<int>(ntiles, sm_count());
   FgTimed timed(kclass, s);
   tc_gemm_kernel<BN, RB, RA><<<grid, Cfg::THREADS, smem_req, s>>>(mA, mB, mT, q);
