@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--serving-scale", default="full", choices=["full", "small"])
     ap.add_argument("--serving-rates", type=float, nargs="+", default=[0.3, 0.6, 0.9, 1.2, 2.0, 4.0],
                     help="arrival rates as fractions of the measured sequential capacity")
+    ap.add_argument("--no-target", action="store_true",
+                    help="skip the N=4096, L=64 leg (single-order assembly, stacked GEMM) of the default run")
+    ap.add_argument("--no-serving", action="store_true", help="skip the small serving sweep of the default run")
     return ap.parse_args()
 
 
@@ -224,15 +227,19 @@ def run_reference(args):
     ora = OracleOnline(wl)
     for k in range(args.warmup):
         ora.run(1e9, max_orders=sample, start=sample * k)
-    times = []
+    times, step_s = [], []
     for k in range(args.steps):
         done, el, _ = ora.run(1e9, max_orders=sample, start=sample * (k + args.warmup))
         times.append(el / done)
+        step_s.append(el)
     per_order = statistics.mean(times)
     value = 1.0 / per_order
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_order * n_orders * 1e3,
+        "steps": args.steps, "warmup": args.warmup,
+        # a step of this arm is the bounded sample (2 orders x 256 signals): its measured time
+        "ms_per_step": statistics.mean(step_s) * 1e3,
+        "ms_per_full_batch_extrapolated": per_order * n_orders * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": 1024, "L": 32, "orders": n_orders, "signals_per_order": per,
                    "sample_per_step": f"{sample} orders x {per} signals"},
@@ -315,6 +322,16 @@ def run_ours(args):
     t_max = reduce_max(total_ms)
     ms_step = t_max / args.steps
     value = whole_job_rate(n_orders * args.steps, ws, t_max / 1e3)
+    # the same loop without the per-kernel timing events (they add small gaps between
+    # launches): how much the instrumentation of the timed region costs
+    torch.cuda.synchronize()
+    e0n, e1n = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0n.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1n.record(stream)
+    torch.cuda.synchronize()
+    ms_step_noev = reduce_max(e0n.elapsed_time(e1n)) / args.steps
     # the same step on complex64 device buffers
     for _ in range(3):
         step(complex_io=True)
@@ -481,7 +498,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "fp16x3-split tensor GEMM, f32 accumulate; f32 assembly", "data": "synthetic",
+        "dtype": ("fp16 hi/lo split operands x3 products on tcgen05 tensor cores, f32 accumulate (fused "
+                  "multi-order assembly and grouped apply); FP64 offline"), "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "L": L, "orders": n_orders, "signals_per_order": B // n_orders,
                    "path": "assembled (fused multi-order assembly + tcgen05 grouped GEMM)",
                    "signals": ("real float32 signals and outputs (FGFRFT_REAL_SIGNALS / _REAL_OUTPUT)"
@@ -489,11 +507,17 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (stack 545 MB c64 + assembled operators 537 MB per step)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "signals_per_s": whole_job_rate(B * args.steps, ws, t_max / 1e3),
+        "ms_per_step_without_kernel_events": ms_step_noev,
         "complex64_buffers": {"ms_per_step": ms_step_c, "value": n_orders / (ms_step_c / 1e3) * ws},
         "graph_replay": graph_replay,
         "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99))},
         "plain_fp32": {"ms_per_step": plain_ms, "order_updates_per_s": n_orders / (plain_ms / 1e3),
-                       "speedup_vs_plain": plain_ms / ms_step,
+                       "io": "complex64 device buffers",
+                       # the like-for-like pairing: both paths on complex64 buffers
+                       "speedup_vs_plain": plain_ms / ms_step_c,
+                       "speedup_vs_plain_pairing": "optimized step on complex64 buffers vs plain path on "
+                                                   "complex64 buffers",
+                       "speedup_headline_real_io_vs_plain": plain_ms / ms_step,
                        "assemble_single": {"launches": n1, "avg_us": 1e3 * ms1 / max(t1, 1),
                                            "bytes_per_launch": k1_bytes, "achieved_gbs": k1_gbs,
                                            "frac_of_hbm": (k1_gbs / peaks.get("hbm_gbs", 6800.0)) if k1_gbs else None},
@@ -515,11 +539,201 @@ def run_ours(args):
                                           f"numpy (Algorithm 1 with stored powers, then Q X); offline excluded",
                                 "rel_err_gpu_vs_fp64": err}
         line["rel_err_vs_fp64"] = err
+    # ---- the other legs of the default run (one GPU only: a scaling run times the headline)
+    if ws == 1:
+        del plan
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        if not args.no_target:
+            line["target_n4096_l64"] = leg_target(args, local)
+        if not args.no_serving:
+            line["serving_small"] = leg_serving(args, local, scale="small", requests=2000, rates=[0.6, 2.0])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+# ----------------------------------------------------------------------------- default-run legs
+def _events_ms(fn, steps, warmup):
+    """Device time per call of fn on the current stream (CUDA events), after warmup calls."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _kernel_ms(FG, cls, fn, steps, warmup):
+    """(mean CUDA-event time per launch of kernel class cls, launches) while fn runs steps times."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    FG.timing_reset()
+    FG.timing_enable(True)
+    for _ in range(steps):
+        fn()
+    torch.cuda.synchronize()
+    FG.timing_enable(False)
+    n, t, ms = FG.timing_read()[cls]
+    return ms / max(t, 1), n
+
+
+def _oracle_projector_for(F):
+    """FP64 P for the oracle comparisons: real eigenvalues certify r_-1 = 0 cheaply (P = 0)."""
+    import scipy.linalg
+    from oracle import fgfrft_oracle as O
+    lam = scipy.linalg.eigvals(F.real if not np.any(F.imag) else F)
+    if np.min(np.abs(lam + 1.0)) > 1e-6:
+        return np.zeros(F.shape, dtype=np.complex128)
+    return O.projector(F)
+
+
+def leg_target(args, gpu_index):
+    """The target configuration, N = 4096 (4096-point RGG), L = 64, 1024 complex signals:
+    single-order assembly from the half stack (K1h) and from the full real split stack (K1r)
+    against the HBM roof; the stacked split GEMM with per-column orders against the tensor
+    roof; the assembled (one shared order) and plain FP32 paths; each with its error against
+    the FP64 oracle on sampled columns.  Offline precompute outside the timed regions."""
+    import torch
+    from paper_2602_20870_gb300 import fgfrft as FG
+    from paper_2602_20870_gb300 import workloads as W
+    wl = W.precision()
+    N, L, B = wl.N, wl.L, wl.B
+    peaks, src = measured_peaks()
+    hpeak = peaks.get("hbm_gbs", 6800.0)
+    tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
+    out = {"workload": wl.name, "orders": "per column U[-2, 2] (stacked); 0.37 shared (assembled, plain)"}
+    t0 = time.perf_counter()
+    half = FG.Plan(wl.F, L, storage=FG.STORE_HALF | FG.STORE_SPLIT_F16)
+    out["offline_precompute_s_half_plus_split"] = time.perf_counter() - t0
+    X = torch.as_tensor(wl.X, dtype=torch.complex64).cuda()
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    time.sleep(0.3)
+    # K1h: one order from the half stack (L + 2 blocks read as pairs of transposed tiles)
+    ms, n = _kernel_ms(FG, "assemble_single", lambda: half.assemble([0.37], L), 10, 3)
+    byts = (4.0 if half.real else 8.0) * (L + 1 + (1 if half.r_neg1 > 0 else 0)) * N * N + 8.0 * N * N
+    out["assemble_single_half"] = {
+        "kernel": "assemble_half_kernel", "bound": "hbm", "avg_launch_ms": ms, "launches": n,
+        "order_updates_per_s": 1e3 / ms, "algorithmic_bytes_per_launch": byts,
+        "achieved_gbs": byts / (ms * 1e-3) / 1e9, "peak_gbs": hpeak,
+        "frac_of_hbm": byts / (ms * 1e-3) / 1e9 / hpeak, "peak_source": f"{src} hbm_gbs"}
+    # per-column orders on the stacked split GEMM (all 130 stored blocks as K-major operands)
+    ms_st = _events_ms(lambda: half.apply(wl.alpha, X, L, path="stacked"), 4, 1)
+    kst, nst = _kernel_ms(FG, "tc_gemm", lambda: half.apply(wl.alpha, X, L, path="stacked"), 3, 0)
+    fl = (4.0 if half.real else 8.0) * (2 * L + 2) * N * N * B  # algorithmic (real F: real x complex)
+    out["stacked_per_column"] = {
+        "kernel": "tc_gemm_kernel<128> (stacked)", "bound": "tensor", "ms_per_call": ms_st,
+        "signals_per_s": B / (ms_st * 1e-3), "gemm_avg_launch_ms": kst,
+        "algorithmic_flops": fl, "algorithmic_tflops": fl / (kst * 1e-3) / 1e12,
+        "executed_tensor_tflops": 3 * fl / (kst * 1e-3) / 1e12,
+        "tensor_frac_executed": 3 * fl / (kst * 1e-3) / 1e12 / tpeak,
+        "tensor_frac_algorithmic": fl / (kst * 1e-3) / 1e12 / tpeak,
+        "peak_tflops": tpeak, "peak_source": f"{src} bf16_tflops_sustained (fp16 dense rate equals bf16)"}
+    Ys = half.apply(wl.alpha, X, L, path="stacked").cpu().numpy()
+    shared = np.full(B, 0.37)
+    ms_as = _events_ms(lambda: half.apply(shared, X, L, path="assembled"), 4, 1)
+    Ya = half.apply(shared, X, L, path="assembled").cpu().numpy()
+    ms_pl = _events_ms(lambda: half.apply(shared, X, L, path="plain"), 3, 1)
+    Yp = half.apply(shared, X, L, path="plain").cpu().numpy()
+    out["assembled_shared"] = {"ms_per_call": ms_as, "signals_per_s": B / (ms_as * 1e-3)}
+    out["plain_fp32_shared"] = {"ms_per_call": ms_pl, "signals_per_s": B / (ms_pl * 1e-3)}
+    out["clocks_half_and_gemm"] = clk.stop()
+    del half
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    # K1r: one order from the full stack's two real split planes (2L + 2 blocks)
+    t0 = time.perf_counter()
+    split = FG.Plan(wl.F, L, storage=FG.STORE_SPLIT_F16)
+    out["offline_precompute_s_split"] = time.perf_counter() - t0
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    time.sleep(0.3)
+    ms, n = _kernel_ms(FG, "assemble_single", lambda: split.assemble([0.37], L), 10, 3)
+    byts = (4.0 if split.real else 8.0) * (2 * L + 2) * N * N + 8.0 * N * N
+    out["assemble_single_full"] = {
+        "kernel": "assemble_single_real_kernel" if split.real else "assemble_single_kernel", "bound": "hbm",
+        "avg_launch_ms": ms, "launches": n, "order_updates_per_s": 1e3 / ms, "algorithmic_bytes_per_launch": byts,
+        "achieved_gbs": byts / (ms * 1e-3) / 1e9, "peak_gbs": hpeak,
+        "frac_of_hbm": byts / (ms * 1e-3) / 1e9 / hpeak, "peak_source": f"{src} hbm_gbs"}
+    out["clocks_full"] = clk.stop()
+    del split
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if not args.no_cpu_baseline:
+        from oracle import fgfrft_oracle as O
+        t0 = time.perf_counter()
+        P = _oracle_projector_for(wl.F)
+        cols = np.arange(0, B, 128)
+        ref_s = O.apply_power(wl.F, wl.alpha[cols], L, wl.X[cols].T, P).T
+        ref_1 = O.apply_power(wl.F, 0.37, L, wl.X[cols].T, P).T
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        out["rel_err_vs_fp64"] = {"stacked_split (bar 5e-5)": rel(Ys[cols], ref_s),
+                                  "assembled_split (bar 5e-5)": rel(Ya[cols], ref_1),
+                                  "plain_fp32 (bar 1e-5)": rel(Yp[cols], ref_1),
+                                  "sample": f"{len(cols)} of {B} columns, FP64 oracle (signal recursion)",
+                                  "oracle_s": time.perf_counter() - t0}
+    return out
+
+
+def leg_serving(args, gpu_index, scale="small", requests=2000, rates=(0.6, 2.0)):
+    """Continuous batching against the plain one-request-at-a-time FP32 path (a short sweep)."""
+    import torch
+    from paper_2602_20870_gb300 import fgfrft as FG
+    from paper_2602_20870_gb300 import serving as S
+    from paper_2602_20870_gb300 import workloads as W
+    sizes = [256, 512, 1024, 1024, 2048, 2048, 4096, 4096] if scale == "full" else \
+        [64, 128, 256, 256, 512, 512, 1024, 1024]
+    L_max = 64 if scale == "full" else 32
+    Ls = (16, 32, 64) if L_max == 64 else (8, 16, 32)
+    t0 = time.perf_counter()
+    plans = [FG.Plan(W.rgg_gft(n, 500 + i), L_max, storage=FG.STORE_C64 | FG.STORE_SPLIT_F16)
+             for i, n in enumerate(sizes)]
+    offline_s = time.perf_counter() - t0
+    resident = sum(p.plan_bytes for p in plans)
+    budget = 150 * 2 ** 30
+    sample = W.serving_requests(sizes, 200, rate_per_s=1e9, seed=55, Ls=Ls, lazy=True)
+    S.sequential(plans, sample[:20], time_scale=0.0)
+    t0 = time.perf_counter()
+    S.sequential(plans, sample, time_scale=0.0)
+    capacity = len(sample) / (time.perf_counter() - t0)
+    sweep = []
+    for frac in rates:
+        reqs = W.serving_requests(sizes, requests, rate_per_s=frac * capacity, seed=5, Ls=Ls, lazy=True)
+        srv = S.Server(plans, budget - resident, max_cols=512, max_inflight_per_graph=2)
+        clk = ClockSampler(gpu_index)
+        clk.start()
+        t0 = time.perf_counter()
+        res = S.replay(srv, reqs, timeout_s=3600)
+        torch.cuda.synchronize()
+        span = time.perf_counter() - t0
+        clocks_b = clk.stop()
+        clk = ClockSampler(gpu_index)
+        clk.start()
+        seq = S.sequential(plans, reqs)
+        clocks_s = clk.stop()
+        seq_span = max(r.done for r in seq)
+        sweep.append({"rate_frac_of_capacity": frac, "rate_per_s": frac * capacity,
+                      "batched": {**S.latency_stats(res), "throughput_rps": len(reqs) / span,
+                                  "launches": srv.launches, "max_reserved_gb": srv.max_reserved / 2 ** 30,
+                                  "clocks": clocks_b},
+                      "sequential_plain": {**S.latency_stats(seq), "throughput_rps": len(reqs) / seq_span,
+                                           "clocks": clocks_s}})
+    del plans
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return {"scale": scale, "graphs": sizes, "L_max": L_max, "requests_per_point": requests,
+            "sequential_capacity_rps": capacity, "resident_plan_gb": resident / 2 ** 30,
+            "offline_precompute_s": offline_s, "sweep": sweep}
 
 
 # ----------------------------------------------------------------------------- other configs
@@ -555,6 +769,9 @@ def run_point_cloud(args):
     X = torch.as_tensor(wl.X, dtype=torch.complex64).cuda()
     G = torch.as_tensor(W.complex_normal(wl.X.shape, np.random.default_rng(3)), dtype=torch.complex64).cuda()
     out = {}
+    clk = ClockSampler(0)
+    clk.start()
+    time.sleep(0.3)
     for path in ("stacked", "stacked_fp32"):
         def step():
             Y, D = plan.forward_dual(wl.alpha, X, L, path=path)
@@ -563,7 +780,7 @@ def run_point_cloud(args):
         flops = 3 * 8.0 * (2 * L + 2) * N * N * B  # forward (dual) + adjoint, algorithmic
         out[path] = {"ms_per_step": ms, "signals_per_s": B / (ms / 1e3), "algorithmic_tflops": flops / ms / 1e9}
     line = {"metric": "signals/s (forward + dY/dalpha + adjoint + alpha-gradient)", "workload": wl.name,
-            "value": out["stacked"]["signals_per_s"], "unit": "signals/s", "paths": out}
+            "value": out["stacked"]["signals_per_s"], "unit": "signals/s", "paths": out, "clocks": clk.stop()}
     if not args.no_cpu_baseline:
         from oracle import fgfrft_oracle as O
         cols = np.arange(0, B, 47)
@@ -583,119 +800,25 @@ def run_point_cloud(args):
 
 
 def run_precision(args):
-    """Precision config (N = 4096, L = 64, 1024 columns): per-column orders on the stacked
-    tensor-core path, one shared order on the assembled tensor path and on the plain FP32
-    path, each with its error against the FP64 oracle on sampled columns."""
-    import torch
+    """Precision config (N = 4096, L = 64, 1024 columns): the default run's target leg alone."""
     from paper_2602_20870_gb300 import build as BUILD
     BUILD.build()
-    from paper_2602_20870_gb300 import fgfrft as FG
-    from paper_2602_20870_gb300 import workloads as W
-    wl = W.precision()
-    N, L, B = wl.N, wl.L, wl.B
-    t0 = time.perf_counter()
-    plan = FG.Plan(wl.F, L)
-    offline_s = time.perf_counter() - t0
-    X = torch.as_tensor(wl.X, dtype=torch.complex64).cuda()
-    res = {}
-    outs = {}
-    cases = [("stacked", wl.alpha, "stacked"), ("assembled_shared", np.full(B, 0.37), "assembled"),
-             ("plain_shared", np.full(B, 0.37), "plain")]
-    for name, a, path in cases:
-        ms = _device_time(lambda: plan.apply(a, X, L, path=path), max(2, args.steps // 4), 2)
-        outs[name] = plan.apply(a, X, L, path=path).cpu().numpy()
-        res[name] = {"ms": ms, "signals_per_s": B / (ms / 1e3)}
-    # single-order assembly at this size (17.6 GB streamed per order)
-    FG.timing_reset()
-    FG.timing_enable(True)
-    ms1 = _device_time(lambda: plan.assemble([0.37], L), 5, 2)
-    FG.timing_enable(False)
-    n1, t1, k1 = FG.timing_read()["assemble_single"]
-    byts = (4.0 if plan.real else 8.0) * (2 * L + 2) * N * N + 8.0 * N * N
-    peaks, src = measured_peaks()
-    res["assemble_single"] = {"ms": k1 / max(t1, 1), "order_updates_per_s": 1e3 / (k1 / max(t1, 1)),
-                              "achieved_gbs": byts / (k1 / max(t1, 1) * 1e-3) / 1e9,
-                              "frac_of_hbm": byts / (k1 / max(t1, 1) * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
-    # the same order from the half stack (M_0..M_L and P only; M_{-l} read as transposed tiles)
-    Qf = plan.assemble([0.37], L)
-    half = FG.Plan(wl.F, L, storage=FG.STORE_HALF)
-    FG.timing_reset()
-    FG.timing_enable(True)
-    _device_time(lambda: half.assemble([0.37], L), 5, 2)
-    FG.timing_enable(False)
-    n1, t1, k1 = FG.timing_read()["assemble_single"]
-    byts_h = (4.0 if half.real else 8.0) * (L + 1 + (1 if half.r_neg1 > 0 else 0)) * N * N + 8.0 * N * N
-    Qh = half.assemble([0.37], L)
-    res["assemble_single_half"] = {
-        "ms": k1 / max(t1, 1), "order_updates_per_s": 1e3 / (k1 / max(t1, 1)),
-        "achieved_gbs": byts_h / (k1 / max(t1, 1) * 1e-3) / 1e9,
-        "frac_of_hbm": byts_h / (k1 / max(t1, 1) * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
-        "stack_gb": half.plan_bytes / 1e9, "full_stack_gb": plan.plan_bytes / 1e9,
-        "rel_diff_vs_full_storage": float(torch.linalg.norm(Qh - Qf) / torch.linalg.norm(Qf))}
-    del half, Qh, Qf
-    line = {"metric": "signals/s and order-updates/s", "workload": wl.name, "unit": "signals/s",
-            "value": res["stacked"]["signals_per_s"], "paths": res, "offline_precompute_s": offline_s}
-    if not args.no_cpu_baseline:
-        from oracle import fgfrft_oracle as O
-        import scipy.linalg
-        lam = scipy.linalg.eigvals(wl.F.real)
-        P = np.zeros((N, N), complex) if np.min(np.abs(lam + 1)) > 1e-6 else O.projector(wl.F)
-        cols = np.arange(0, B, 128)
-        t0 = time.perf_counter()
-        refs = {"stacked": O.apply_power(wl.F, wl.alpha[cols], L, wl.X[cols].T, P).T}
-        el = time.perf_counter() - t0
-        refs["assembled_shared"] = refs["plain_shared"] = O.apply_power(wl.F, 0.37, L, wl.X[cols].T, P).T
-        line["cpu_baseline"] = {"value": len(cols) / el, "unit": "signals/s", "cores": cpu_cores(), "kind": "oracle",
-                                "sample": f"{len(cols)} columns (signal recursion, no stored powers)"}
-        line["rel_err_vs_fp64"] = {k: _rel(outs[k][cols], refs[k]) for k in refs}
+    out = leg_target(args, 0)
+    line = {"metric": "signals/s and order-updates/s", "unit": "signals/s",
+            "value": out["stacked_per_column"]["signals_per_s"], **out}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def run_serving(args):
     """Serving config: Poisson arrivals over 8 resident graphs, continuous batching against
-    the plain one-request-at-a-time FP32 path, at 0.3 .. 1.2 x the sequential capacity."""
-    import torch
+    the plain one-request-at-a-time FP32 path, at the given fractions of the sequential
+    capacity (clocks recorded during each timed run)."""
     from paper_2602_20870_gb300 import build as BUILD
     BUILD.build()
-    from paper_2602_20870_gb300 import fgfrft as FG
-    from paper_2602_20870_gb300 import serving as S
-    from paper_2602_20870_gb300 import workloads as W
-    sizes = [256, 512, 1024, 1024, 2048, 2048, 4096, 4096] if args.serving_scale == "full" else \
-        [64, 128, 256, 256, 512, 512, 1024, 1024]
-    L_max = 64 if args.serving_scale == "full" else 32
-    Ls = (16, 32, 64) if L_max == 64 else (8, 16, 32)
-    t0 = time.perf_counter()
-    # serving uses the stacked (per-request order) paths: c64 + split planes, no entry-major copy
-    plans = [FG.Plan(W.rgg_gft(n, 500 + i), L_max, storage=FG.STORE_C64 | FG.STORE_SPLIT_F16)
-             for i, n in enumerate(sizes)]
-    offline_s = time.perf_counter() - t0
-    resident = sum(p.plan_bytes for p in plans)
-    budget = 150 * 2 ** 30
-    # sequential capacity from a sample run back to back
-    sample = W.serving_requests(sizes, 200, rate_per_s=1e9, seed=55, Ls=Ls, lazy=True)
-    S.sequential(plans, sample[:20], time_scale=0.0)
-    t0 = time.perf_counter()
-    S.sequential(plans, sample, time_scale=0.0)
-    capacity = len(sample) / (time.perf_counter() - t0)
-    sweep = []
-    for frac in args.serving_rates:
-        reqs = W.serving_requests(sizes, args.serving_requests, rate_per_s=frac * capacity, seed=5, Ls=Ls, lazy=True)
-        srv = S.Server(plans, budget - resident, max_cols=512, max_inflight_per_graph=2)
-        t0 = time.perf_counter()
-        res = S.replay(srv, reqs, timeout_s=3600)
-        torch.cuda.synchronize()
-        span = time.perf_counter() - t0
-        seq = S.sequential(plans, reqs)
-        seq_span = max(r.done for r in seq)
-        sweep.append({"rate_frac_of_capacity": frac, "rate_per_s": frac * capacity,
-                      "batched": {**S.latency_stats(res), "throughput_rps": len(reqs) / span,
-                                  "launches": srv.launches, "max_reserved_gb": srv.max_reserved / 2 ** 30},
-                      "sequential_plain": {**S.latency_stats(seq), "throughput_rps": len(reqs) / seq_span}})
+    out = leg_serving(args, 0, scale=args.serving_scale, requests=args.serving_requests, rates=args.serving_rates)
     line = {"metric": "serving p50/p99 latency and throughput vs plain sequential FP32", "unit": "requests/s",
-            "value": sweep[-1]["batched"]["throughput_rps"], "graphs": sizes, "L_max": L_max,
-            "requests_per_point": args.serving_requests, "sequential_capacity_rps": capacity,
-            "resident_plan_gb": resident / 2 ** 30, "offline_precompute_s": offline_s, "sweep": sweep}
+            "value": out["sweep"][-1]["batched"]["throughput_rps"], **out}
     print(json.dumps(line), flush=True)
     return 0
 

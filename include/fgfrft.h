@@ -136,7 +136,7 @@ int fgfrft_version(void);
  * FGFRFT_STORE_ENTRY_F16 without FGFRFT_STORE_SPLIT_F16). */
 size_t fgfrft_plan_bytes(int64_t N, int L_max, int storage);
 
-/* Bytes of FP64 device scratch fgfrft_precompute needs: 3 N^2 complex128
+/* Bytes of FP64 device scratch fgfrft_precompute needs: 4 N^2 complex128
  * matrices plus a reduction area. */
 size_t fgfrft_precompute_work_bytes(int64_t N);
 
@@ -148,34 +148,62 @@ size_t fgfrft_precompute_work_bytes(int64_t N);
  *   W_dev       optional N x r complex128 row-major matrix with orthonormal
  *               columns spanning the lambda = -1 eigenspace (Algorithm 1,
  *               "form W"); NULL lets the library find the eigenspace itself:
- *               S = (I - F)(I - F)^H / 4 has eigenvalues sin^2(theta_k / 2),
- *               equal to 1 exactly on the lambda = -1 eigenspace; repeated
- *               squaring of S followed by McWeeny purification P <- 3P^2 - 2P^3
- *               gives P.  Eigenvalues within ~3e-8 of -1 count as -1; one
- *               that squaring cannot separate in 46 steps gives
- *               FGFRFT_ERR_AMBIGUOUS_SPECTRUM.
+ *               S = (I - F)(I - F)^H / 4 has eigenvalues s_k = sin^2(theta_k / 2)
+ *               = 1 - |lambda_k + 1|^2 / 4, equal to 1 exactly on the lambda = -1
+ *               eigenspace; repeated squaring of S followed by McWeeny
+ *               purification P <- 3P^2 - 2P^3 gives P (Sec. III-B: I_{-1} = {k :
+ *               theta_k = pi}; the paper fixes no tolerance for it).
  *   r_W         number of columns of W_dev (ignored when W_dev is NULL).
+ *   neg1_tol    which eigenvalues count as -1 when W_dev is NULL:
+ *               0: adaptive.  S is squared until its powers separate into the
+ *                  two basins of McWeeny's iteration (at most 2^46-th power), so
+ *                  the widest gap in |lambda + 1| below that scale decides.  The
+ *                  call then refuses (FGFRFT_ERR_AMBIGUOUS_SPECTRUM) a spectrum
+ *                  with an eigenvalue in the band FP64 cannot certify: one left in
+ *                  the complement closer than 1e-6 to -1 (min_gap below), or one
+ *                  counted as -1 whose |lambda + 1| exceeds the rounding level of
+ *                  P (max(1e-9, 256 u N / min_gap), u = 2^-53, and at most 1e-6),
+ *                  measured by proj_residual / sqrt(r_neg1).
+ *               in [1e-6, 0.5]: fixed threshold.  S is squared exactly
+ *                  ceil(log2(4 ln 2 / neg1_tol^2)) times, which takes an eigenvalue
+ *                  with |lambda + 1| = neg1_tol to at most 1/2; eigenvalues below
+ *                  about 0.28 x that boundary count as -1, those above about 2.06 x
+ *                  it do not (the boundary lies in (neg1_tol / sqrt 2, neg1_tol]),
+ *                  and one in between returns FGFRFT_ERR_AMBIGUOUS_SPECTRUM.
+ *               Any other value: FGFRFT_ERR_INVALID_ARG.  Ignored with W_dev.
+ *   P_dev       optional N x N complex128 device output: the FP64 projector P
+ *               before it is rounded into storage (16-byte aligned; NULL: not
+ *               written).
  *   plan_mem    device buffer of at least fgfrft_plan_bytes(N, L_max, storage)
  *               bytes, 256-byte aligned; it holds the plan for its lifetime.
  *   work        device scratch of fgfrft_precompute_work_bytes(N) bytes,
  *               256-byte aligned; free again when the call returns.
  *   out         receives the plan handle (a small host record; release it
  *               with fgfrft_plan_destroy).
- * Checks ||F^H F - I||_F / sqrt(N) <= 1e-8 (FGFRFT_ERR_NOT_UNITARY).
+ * Checks ||F^H F - I||_F / sqrt(N) <= 1e-8 (FGFRFT_ERR_NOT_UNITARY).  A real F
+ * (every imaginary part exactly 0, no W) is processed with real FP64 products.
  * Synchronises the stream (it reads traces back to the host).
  */
 int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage,
-                      const double* W_dev, int64_t r_W,
+                      const double* W_dev, int64_t r_W, double neg1_tol, double* P_dev,
                       void* plan_mem, size_t plan_bytes,
                       void* work, size_t work_bytes,
                       void* stream, fgfrft_plan* out);
 
 /* Plan metadata; any output pointer may be NULL.
  *   r_neg1         rank of P (the multiplicity of lambda = -1).
- *   proj_residual  ||F P + P||_F after precompute (0 when r_neg1 = 0).
- *   squarings      squaring steps the projector needed (0 when W was given). */
+ *   proj_residual  ||F P + P||_F after precompute (0 when r_neg1 = 0); for the
+ *                  exact projector it is sqrt(sum over the counted eigenvalues of
+ *                  |lambda_k + 1|^2).
+ *   squarings      squaring steps the projector needed (0 when W was given).
+ *   min_gap        two doubles: a lower and an upper bound of
+ *                  min_{k not in I_-1} |lambda_k + 1| = 2 cos_{c,min} (the distance
+ *                  of the nearest complementary eigenvalue from -1, Thm. 2), from
+ *                  the traces of repeated squares of the complement part of S;
+ *                  upper / lower <= 1.01 unless the 2^52-th power was reached
+ *                  first; both +inf when every eigenvalue is -1. */
 int fgfrft_plan_info(fgfrft_plan p, int64_t* N, int* L_max, int* storage, int* r_neg1,
-                     double* proj_residual, int* squarings, size_t* plan_bytes);
+                     double* proj_residual, int* squarings, size_t* plan_bytes, double* min_gap);
 
 /* Device pointer to stored block l (-L_max <= l <= L_max, or l = L_max + 1 for
  * P) in the given storage (one bit), and the element stride between blocks.
@@ -242,7 +270,10 @@ int fgfrft_apply(fgfrft_plan p, const double* alpha_host, int64_t B, int L,
  * Backward (G_dev != NULL), G = dloss/dRe(Y) + j dloss/dIm(Y):
  *   gradX = (Q_L^{alpha_j})^H G[:, j] (if gradX_dev; Prop. 2), and
  *   gradalpha[j] = Re sum_i conj(G_ij) D_ij (if gradalpha_dev), with D read
- *   from dY_dev (computed in this call or an earlier one).
+ *   from dY_dev (computed in this call or an earlier one).  With
+ *   FGFRFT_SHARED_ALPHA (alpha_host holds one order for every column) the
+ *   gradient of that one order is written: gradalpha[0] = sum_j of the above
+ *   (FP64 partial sums added in a fixed order, one float written).
  * Paths: FGFRFT_PATH_STACKED (default with FGFRFT_STORE_SPLIT_F16) or
  * FGFRFT_PATH_STACKED_FP32.
  */
@@ -299,7 +330,10 @@ int fgfrft_check_wait_timeout(fgfrft_plan p, void* stream);
  * FGFRFT_ERR_UNSUPPORTED before anything is enqueued.  The call allocates nothing:
  * no cudaMalloc, cudaFree or allocating library routine.  Its first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture.  All calls
+ * device current) and keeps it for the life of the process; make that first call
+ * before any stream capture.  A cudaDeviceReset (or any other teardown of the
+ * device's primary context) invalidates the kept address: do not call this entry
+ * point on a device after resetting it in the same process.  All calls
  * share the one array and every call overwrites the part it uses, so calls that
  * overlap on the GPU (different streams without ordering) race.
  */

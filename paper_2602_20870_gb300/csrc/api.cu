@@ -147,6 +147,23 @@ struct Carve {
 
 constexpr int kAssembledMinRun = 64;
 
+// Classification of the lambda = -1 eigenvalues (offline projector).
+constexpr int kMaxSquarings = 46;           // adaptive route: at most 2^46-th power of S
+constexpr double kNeg1TolMin = 1e-6;        // fixed threshold: FP64 resolves 1 - g^2/4 down to here
+constexpr double kNeg1TolMax = 0.5;
+constexpr double kAmbiguousGap = 1e-6;      // adaptive route: complement eigenvalues closer to -1 are refused
+constexpr double kResidualFloor = 1e-9;     // adaptive route: |lambda + 1| of the counted eigenvalues below this
+constexpr double kGapBracket = 1.01;        // min_gap bracket: upper / lower bound at most this
+constexpr int kMaxGapPower = 52;            // ... or the bracket of S^(2^52), whichever comes first
+
+// Squarings that take s = 1 - tol^2/4 to at most 1/2: 2^m >= 4 ln 2 / tol^2.
+int squarings_for_tol(double tol) {
+  const double x = 4.0 * 0.6931471805599453 / (tol * tol);
+  int m = 0;
+  while (ldexp(1.0, m) < x && m < 60) ++m;
+  return std::max(m, 1);
+}
+
 int choose_path(const fgfrft_plan_s* p, const Runs& runs, int flags) {
   int path = flags & FGFRFT_PATH_MASK;
   if (path) return path;
@@ -406,12 +423,12 @@ size_t fgfrft_plan_bytes(int64_t N, int L_max, int storage) {
 
 size_t fgfrft_precompute_work_bytes(int64_t N) {
   if (N < 1 || N > 65536) return 0;
-  return align_up((size_t)3 * N * N * sizeof(double2)) + kAlign;
+  return align_up((size_t)4 * N * N * sizeof(double2)) + kAlign;
 }
 
 int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, const double* W_dev, int64_t r_W,
-                      void* plan_mem, size_t plan_bytes, void* work, size_t work_bytes, void* stream,
-                      fgfrft_plan* out) {
+                      double neg1_tol, double* P_dev, void* plan_mem, size_t plan_bytes, void* work,
+                      size_t work_bytes, void* stream, fgfrft_plan* out) {
   if (!out) return FGFRFT_ERR_INVALID_ARG;
   *out = nullptr;
   const size_t need = fgfrft_plan_bytes(N, L_max, storage);
@@ -419,6 +436,8 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   if (work_bytes < fgfrft_precompute_work_bytes(N)) return FGFRFT_ERR_INVALID_ARG;
   if (!aligned(plan_mem) || !aligned(work) || !aligned(F_dev, 16)) return FGFRFT_ERR_INVALID_ARG;
   if (W_dev && (r_W < 0 || r_W > N || !aligned(W_dev, 16))) return FGFRFT_ERR_INVALID_ARG;
+  if (P_dev && !aligned(P_dev, 16)) return FGFRFT_ERR_INVALID_ARG;
+  if (!(neg1_tol == 0.0 || (neg1_tol >= kNeg1TolMin && neg1_tol <= kNeg1TolMax))) return FGFRFT_ERR_INVALID_ARG;
   if (N > 46340) return FGFRFT_ERR_UNSUPPORTED;  // int GEMM indices
   cudaStream_t s = (cudaStream_t)stream;
   const Layout lay = plan_layout(N, L_max, storage);
@@ -451,7 +470,8 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   double2* Am = (double2*)work;
   double2* Bm = Am + N * N;
   double2* Cm = Bm + N * N;
-  double* red = (double*)((char*)work + align_up((size_t)3 * N * N * sizeof(double2)));
+  double2* Dm = Cm + N * N;
+  double* red = (double*)((char*)work + align_up((size_t)4 * N * N * sizeof(double2)));
   double h[3];
   auto fail = [&](int code) {
     free(p);
@@ -473,8 +493,15 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   // exact zero imaginary parts), so the tensor-core paths may skip the imaginary planes
   if (fg_zimag_sq(N, (const double2*)F_dev, red, s) || !readback()) return fail(FGFRFT_ERR_CUDA);
   p->real = (h[0] == 0.0) && (!W_dev);
+  // real F: every FP64 product below is of real matrices, formed by the real GEMM (the same
+  // values in a quarter of the FP64 work)
+  const bool rg = p->real;
+  auto gemm = [&](bool ta, bool tb, double2 alpha, const double2* A, const double2* B, double2* C) {
+    return fg_zgemm(ta, tb, n, n, n, alpha, A, n, B, n, zero, C, n, s, rg);
+  };
 
-  // (2) projector P onto the lambda = -1 eigenspace, into Cm
+  // (2) projector P onto the lambda = -1 eigenspace, into Cm.  The route without W leaves
+  // S^(2^squarings) in Dm for the gap estimate below.
   int squarings = 0;
   if (W_dev) {
     if (r_W > 0) {
@@ -485,31 +512,39 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
       return fail(FGFRFT_ERR_CUDA);
     }
   } else {
-    // T = (I - F)/2 -> Am;  S = T T^H -> Bm  (eigenvalues sin^2(theta_k/2))
+    // T = (I - F)/2 -> Am;  S = T T^H -> Bm  (eigenvalues s_k = sin^2(theta_k/2) = 1 - |lambda_k + 1|^2 / 4)
     if (fg_zaxpby_identity(N, make_double2(-0.5, 0.0), (const double2*)F_dev, zero, make_double2(0.5, 0.0), Am, s) ||
-        fg_zgemm(false, true, n, n, n, one, Am, n, Am, n, zero, Bm, n, s))
+        gemm(false, true, one, Am, Am, Bm))
       return fail(FGFRFT_ERR_CUDA);
     double2* cur = Bm;
     double2* tmp = Am;
     bool converged = false;
-    // Square until every eigenvalue is within the basin of McWeeny purification:
-    // tr(S) - ||S||_F^2 = sum s_k (1 - s_k) < 0.05 puts each s_k below 0.053 or above 0.947.
-    for (squarings = 1; squarings <= 46; ++squarings) {
-      if (fg_zgemm(false, false, n, n, n, one, cur, n, cur, n, zero, tmp, n, s) || fg_zherm_sym(N, tmp, s))
-        return fail(FGFRFT_ERR_CUDA);
+    // After m squarings the eigenvalues are s_k^(2^m) ~ exp(-2^m |lambda_k + 1|^2 / 4).
+    // Adaptive (neg1_tol = 0): square until every eigenvalue is within the basin of McWeeny
+    // purification: tr(S) - ||S||_F^2 = sum s_k (1 - s_k) < 0.05 puts each s_k below 0.053
+    // or above 0.947.  Fixed threshold: square exactly the number of times that takes an
+    // eigenvalue with |lambda + 1| = neg1_tol to at most 1/2 (McWeeny's dividing point),
+    // then require the same separation.
+    const int fixed = neg1_tol > 0.0 ? squarings_for_tol(neg1_tol) : 0;
+    const int max_sq = fixed ? fixed : kMaxSquarings;
+    for (squarings = 1; squarings <= max_sq; ++squarings) {
+      if (gemm(false, false, one, cur, cur, tmp) || fg_zherm_sym(N, tmp, s)) return fail(FGFRFT_ERR_CUDA);
       std::swap(cur, tmp);
       if (fg_ztrace_fro(N, cur, nullptr, red, s) || !readback()) return fail(FGFRFT_ERR_CUDA);
+      if (fixed && squarings < fixed) continue;
       if (h[0] - h[1] < 0.05) {
         converged = true;
         break;
       }
     }
     if (!converged) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
+    if (cudaMemcpyAsync(Dm, cur, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail(FGFRFT_ERR_CUDA);
     // McWeeny purification P <- 3 P^2 - 2 P^3 (quadratic convergence to 0 / 1)
     for (int it = 0; it < 12; ++it) {
-      if (fg_zgemm(false, false, n, n, n, one, cur, n, cur, n, zero, tmp, n, s) ||  // P^2
-          fg_zgemm(false, false, n, n, n, one, tmp, n, cur, n, zero, Cm, n, s) ||   // P^3
-          fg_ztrace_fro(N, tmp, cur, red, s) || !readback())                         // ||P^2 - P||
+      if (gemm(false, false, one, cur, cur, tmp) ||          // P^2
+          gemm(false, false, one, tmp, cur, Cm) ||           // P^3
+          fg_ztrace_fro(N, tmp, cur, red, s) || !readback())  // ||P^2 - P||
         return fail(FGFRFT_ERR_CUDA);
       if (fg_zmcweeny(N, tmp, Cm, cur, s) || fg_zherm_sym(N, cur, s)) return fail(FGFRFT_ERR_CUDA);
       if (sqrt(h[1]) < 1e-13 * sqrt((double)N)) break;
@@ -523,12 +558,76 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   if (p->r_neg1 == 0 && cudaMemsetAsync(Cm, 0, (size_t)N * N * sizeof(double2), s) != cudaSuccess)
     return fail(FGFRFT_ERR_CUDA);
   p->squarings = squarings;
-  // residual ||F P + P||_F
-  if (fg_zgemm(false, false, n, n, n, one, (const double2*)F_dev, n, Cm, n, zero, Am, n, s) ||
-      fg_zaxpby_identity(N, one, Cm, one, zero, Am, s) || fg_ztrace_fro(N, Am, nullptr, red, s) || !readback())
+  // residual ||F P + P||_F = sqrt(sum_{k in I} |lambda_k + 1|^2) for the exact projector
+  if (gemm(false, false, one, (const double2*)F_dev, Cm, Am) || fg_zaxpby_identity(N, one, Cm, one, zero, Am, s) ||
+      fg_ztrace_fro(N, Am, nullptr, red, s) || !readback())
     return fail(FGFRFT_ERR_CUDA);
   p->proj_residual = sqrt(h[1]);
-  if (p->r_neg1 > 0 && !(p->proj_residual <= 1e-6 * sqrt((double)p->r_neg1))) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
+
+  // (2b) the gap of the complement, min_{k not in I} |lambda_k + 1|, bracketed from the
+  // traces of repeated squares of T = S^(2^m) - P (the complement part of S^(2^m); m = 0 and
+  // S = (I - F)(I - F)^H / 4 when W was given).  With mu_k the eigenvalues of T^(2^j) and
+  // x = 2^(m + j): (sum mu^2 / sum mu)^(1/x) <= s_max <= (sum mu)^(1/x), s_max = 1 - g^2/4.
+  if (p->r_neg1 >= N) {
+    p->min_gap_lo = p->min_gap_hi = INFINITY;
+  } else {
+    if (W_dev) {
+      if (fg_zaxpby_identity(N, make_double2(-0.5, 0.0), (const double2*)F_dev, zero, make_double2(0.5, 0.0), Am,
+                             s) ||
+          gemm(false, true, one, Am, Am, Dm))
+        return fail(FGFRFT_ERR_CUDA);
+    }
+    if (fg_zaxpby_identity(N, make_double2(-1.0, 0.0), Cm, one, zero, Dm, s)) return fail(FGFRFT_ERR_CUDA);
+    double2* T = Dm;
+    double2* T2 = Bm;
+    double lnc = 0.0;  // log of the scale c: T^(2^j) = c * (the matrix held in T)
+    const int m0 = W_dev ? 0 : squarings;
+    double glo = 0.0, ghi = 2.0;
+    for (int j = 0;; ++j) {
+      if (fg_ztrace_fro(N, T, nullptr, red, s) || !readback()) return fail(FGFRFT_ERR_CUDA);
+      const double A = h[0], Bq = h[1];
+      const double x = ldexp(1.0, m0 + j);
+      if (!(A > 1e-300) || !(Bq > 0.0)) {  // the complement's powers vanish: every s_k below the bound
+        const double ln_hi = (lnc + log(1e-300)) / x;
+        glo = ln_hi < 0.0 ? 2.0 * sqrt(-expm1(ln_hi)) : 0.0;
+        ghi = 2.0;
+        break;
+      }
+      const double ln_hi = (lnc + log(A)) / x;             // log of the upper bound of s_max
+      const double ln_lo = (lnc + log(Bq) - log(A)) / x;   // log of the lower bound
+      glo = ln_hi < 0.0 ? 2.0 * sqrt(-expm1(ln_hi)) : 0.0;
+      ghi = ln_lo < 0.0 ? 2.0 * sqrt(-expm1(ln_lo)) : 0.0;
+      if ((glo > 0.0 && ghi <= kGapBracket * glo) || m0 + j >= kMaxGapPower) break;
+      // T <- T^2 / ||T||_F^2 (trace 1 for a Hermitian T), c <- c^2 ||T||_F^2
+      if (gemm(false, false, make_double2(1.0 / Bq, 0.0), T, T, T2) || fg_zherm_sym(N, T2, s))
+        return fail(FGFRFT_ERR_CUDA);
+      std::swap(T, T2);
+      lnc = 2.0 * lnc + log(Bq);
+    }
+    p->min_gap_lo = glo;
+    p->min_gap_hi = std::max(glo, ghi);
+  }
+  p->neg1_tol = neg1_tol;
+  // Classification checks.  Every eigenvalue counted as -1 must be -1 to FP64 accuracy
+  // (the residual, above the rounding of P, which grows as u N / gap), and none left in the
+  // complement may lie within kAmbiguousGap of -1: a spectrum with an eigenvalue between
+  // those two scales has no classification that FP64 can certify.  With a fixed threshold
+  // the separation test above already guards the band around neg1_tol.
+  if (p->r_neg1 > 0) {
+    double thr = 1e-6;
+    if (neg1_tol > 0.0 && !W_dev) {
+      thr = neg1_tol;  // the counted eigenvalues lie below ~0.3 neg1_tol (separation test)
+    } else if (!W_dev) {
+      const double u = 1.1102230246251565e-16;
+      thr = std::max(kResidualFloor, 256.0 * u * (double)N / std::max(p->min_gap_lo, 1e-300));
+      thr = std::min(thr, 1e-6);
+    }
+    if (!(p->proj_residual <= thr * sqrt((double)p->r_neg1))) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
+  }
+  if (neg1_tol == 0.0 && !W_dev && p->r_neg1 < N && p->min_gap_lo < kAmbiguousGap)
+    return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
+  if (P_dev && cudaMemcpyAsync(P_dev, Cm, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return fail(FGFRFT_ERR_CUDA);
 
   // (3) powers: M_0 = P_c = I - P, M_n = F M_{n-1}; M_{-n} = M_n^H.  Round into storage.
   auto store = [&](int blk, const double2* M, bool conjT) -> bool {
@@ -548,8 +647,7 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   double2* cur = Am;
   double2* nxt = Bm;
   for (int k = 1; k <= L_max; ++k) {
-    if (fg_zgemm(false, false, n, n, n, one, (const double2*)F_dev, n, cur, n, zero, nxt, n, s))
-      return fail(FGFRFT_ERR_CUDA);
+    if (gemm(false, false, one, (const double2*)F_dev, cur, nxt)) return fail(FGFRFT_ERR_CUDA);
     if (!store(blk_of_power(p, k), nxt, false) || !store(blk_of_power(p, -k), nxt, true) || !store_half(k, nxt))
       return fail(FGFRFT_ERR_CUDA);
     std::swap(cur, nxt);
@@ -562,7 +660,7 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
 }
 
 int fgfrft_plan_info(fgfrft_plan p, int64_t* N, int* L_max, int* storage, int* r_neg1, double* proj_residual,
-                     int* squarings, size_t* plan_bytes) {
+                     int* squarings, size_t* plan_bytes, double* min_gap) {
   if (!p) return FGFRFT_ERR_INVALID_ARG;
   if (N) *N = p->N;
   if (L_max) *L_max = p->L_max;
@@ -571,6 +669,10 @@ int fgfrft_plan_info(fgfrft_plan p, int64_t* N, int* L_max, int* storage, int* r
   if (proj_residual) *proj_residual = p->proj_residual;
   if (squarings) *squarings = p->squarings;
   if (plan_bytes) *plan_bytes = p->bytes;
+  if (min_gap) {
+    min_gap[0] = p->min_gap_lo;
+    min_gap[1] = p->min_gap_hi;
+  }
   return FGFRFT_OK;
 }
 
@@ -888,7 +990,9 @@ int fgfrft_grad(fgfrft_plan p, const double* alpha_host, int64_t B, int L, const
     if (rc) return rc;
   }
   if (G_dev) {
-    if (gradalpha_dev) CK(fg_grad_alpha((const float2*)G_dev, (const float2*)dY_dev, B, p->N, gradalpha_dev, w.partials, s));
+    if (gradalpha_dev)
+      CK(fg_grad_alpha((const float2*)G_dev, (const float2*)dY_dev, B, p->N, gradalpha_dev, w.partials, s,
+                       (flags & FGFRFT_SHARED_ALPHA) != 0));
     if (gradX_dev) {
       std::vector<double> na(a);
       for (auto& v : na) v = -v;

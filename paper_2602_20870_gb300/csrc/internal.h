@@ -33,6 +33,8 @@ struct fgfrft_plan_s {
   int r_neg1;
   double proj_residual;
   int squarings;
+  double min_gap_lo, min_gap_hi;  // bracket of min_{k not in I} |lambda_k + 1| (inf when r_neg1 = N)
+  double neg1_tol;                // 0: adaptive classification
   bool real;           // F (hence every stored block) is real: tensor paths skip the imaginary planes
 };
 
@@ -208,8 +210,11 @@ struct FgTimed {  // records a CUDA event pair around its scope when timing is e
 // launchers (one translation unit each)
 // ---------------------------------------------------------------------------
 // offline.cu
+// real: A and B real (zero imaginary parts), alpha and beta real; a quarter of the FP64
+// work, the same real parts, zero imaginary parts in C.
 cudaError_t fg_zgemm(bool transA, bool transB, int M, int N, int K, double2 alpha, const double2* A, int lda,
-                     const double2* B, int ldb, double2 beta, double2* C, int ldc, cudaStream_t s);
+                     const double2* B, int ldb, double2 beta, double2* C, int ldc, cudaStream_t s,
+                     bool real = false);
 cudaError_t fg_zaxpby_identity(int64_t N, double2 a, const double2* X, double2 b, double2 d, double2* Y,
                                cudaStream_t s);  // Y = a*X + b*Y + d*I
 cudaError_t fg_zherm_sym(int64_t N, double2* S, cudaStream_t s);  // S <- (S + S^H)/2
@@ -278,8 +283,10 @@ cudaError_t fg_simt_stacked(const SimtStackArgs& a, cudaStream_t s);
 cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* coef, float2* coefd, int64_t ldb,
                       int64_t ldj, cudaStream_t s);
 int fg_grad_chunks(int64_t N);
+// out[j] = Re sum_i conj(G_ji) D_ji (FP64 partials per 1024-entry chunk, summed in a fixed
+// order); sum_all: out[0] = the sum over all j (one order shared by every column).
 cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N, float* out, double* partials,
-                          cudaStream_t s);
+                          cudaStream_t s, bool sum_all = false);
 // Split each signal (row of X) into fp16 planes with a per-signal power-of-two scale.
 // bimag (may be NULL) is cleared first and set nonzero when some signal has a nonzero
 // imaginary part.  X is B x N c64, or B x N real float32 when x_real.

@@ -57,7 +57,9 @@ __global__ void noalloc_final_kernel(const double* __restrict__ partial, int nch
   out[j] = (float)s;
 }
 
-// Device address of the fixed scratch on the current device, looked up once per device.
+// Device address of the fixed scratch on the current device, looked up once per device
+// and kept for the life of the process (a device reset in between would leave it stale;
+// the header tells callers not to call this entry point after one).
 int scratch_for_current_device(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FGFRFT_ERR_CUDA;

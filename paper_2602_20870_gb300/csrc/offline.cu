@@ -13,9 +13,13 @@ __device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -
 // C[M x N] = alpha * op(A) op(B) + beta * C, row-major complex128.
 // op(A)[i][k] = A[i][k] or conj(A[k][i]); op(B)[k][j] = B[k][j] or conj(B[j][k]).
 // 64 x 64 output tile per 256-thread block, 4 x 4 entries per thread, k step 16.
+// REAL: A and B have zero imaginary parts and alpha, beta are real; only the real
+// products are formed (a quarter of the FP64 work) and C gets zero imaginary parts.
+// The real parts are the same FP64 values the complex kernel produces (its extra
+// terms are exact zeros).
 constexpr int ZBM = 64, ZBN = 64, ZBK = 16;
 
-template <bool TA, bool TB>
+template <bool TA, bool TB, bool REAL>
 __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, double2 alpha, const double2* __restrict__ A,
                                                     int lda, const double2* __restrict__ B, int ldb, double2 beta,
                                                     double2* __restrict__ C, int ldc) {
@@ -67,6 +71,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, double2
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           acc[r][c].x = fma(a[r].x, b[c].x, acc[r][c].x);
+          if (REAL) continue;
           acc[r][c].x = fma(-a[r].y, b[c].y, acc[r][c].x);
           acc[r][c].y = fma(a[r].x, b[c].y, acc[r][c].y);
           acc[r][c].y = fma(a[r].y, b[c].x, acc[r][c].y);
@@ -81,6 +86,12 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, double2
       const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * c;
       if (gi < M && gj < N) {
         double2* dst = C + (int64_t)gi * ldc + gj;
+        if (REAL) {
+          double v = alpha.x * acc[r][c].x;
+          if (beta.x != 0.0) v += beta.x * dst->x;
+          *dst = make_double2(v, 0.0);
+          continue;
+        }
         double2 v = zmul(alpha, acc[r][c]);
         if (beta.x != 0.0 || beta.y != 0.0) {
           const double2 o = zmul(beta, *dst);
@@ -297,17 +308,27 @@ inline int grid_for(int64_t total) {
 
 }  // namespace
 
-cudaError_t fg_zgemm(bool transA, bool transB, int M, int N, int K, double2 alpha, const double2* A, int lda,
-                     const double2* B, int ldb, double2 beta, double2* C, int ldc, cudaStream_t s) {
-  dim3 grid((N + ZBN - 1) / ZBN, (M + ZBM - 1) / ZBM);
+template <bool REAL>
+void zgemm_launch(bool transA, bool transB, dim3 grid, int M, int N, int K, double2 alpha, const double2* A, int lda,
+                  const double2* B, int ldb, double2 beta, double2* C, int ldc, cudaStream_t s) {
   if (!transA && !transB)
-    zgemm_kernel<false, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    zgemm_kernel<false, false, REAL><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   else if (transA && !transB)
-    zgemm_kernel<true, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    zgemm_kernel<true, false, REAL><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   else if (!transA && transB)
-    zgemm_kernel<false, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    zgemm_kernel<false, true, REAL><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   else
-    zgemm_kernel<true, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    zgemm_kernel<true, true, REAL><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+cudaError_t fg_zgemm(bool transA, bool transB, int M, int N, int K, double2 alpha, const double2* A, int lda,
+                     const double2* B, int ldb, double2 beta, double2* C, int ldc, cudaStream_t s, bool real) {
+  if (real && (alpha.y != 0.0 || beta.y != 0.0)) return cudaErrorInvalidValue;
+  dim3 grid((N + ZBN - 1) / ZBN, (M + ZBM - 1) / ZBM);
+  if (real)
+    zgemm_launch<true>(transA, transB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+  else
+    zgemm_launch<false>(transA, transB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
   fg_note_launch(FGFRFT_KC_OFFLINE);
   return cudaGetLastError();
 }

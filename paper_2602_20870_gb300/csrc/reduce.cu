@@ -175,11 +175,13 @@ __global__ void __launch_bounds__(256) coeff_planes_kernel(const double* __restr
 constexpr int GR_CHUNK = 4096;
 
 // level 1: partial[j][chunk] = Re sum_{i in chunk} conj(G_ji) D_ji   (FP64)
+// (one CTA per (signal j = blockIdx.x, chunk = blockIdx.y); with out != NULL and one chunk
+// the value goes to out[j] directly)
 __global__ void __launch_bounds__(256) grad_partial_kernel(const float2* __restrict__ G,
                                                            const float2* __restrict__ D, int64_t N, int nchunks,
                                                            double* __restrict__ partial, float* __restrict__ out) {
-  const int64_t j = blockIdx.y;
-  const int ch = blockIdx.x;
+  const int64_t j = blockIdx.x;
+  const int ch = blockIdx.y;
   const int64_t i0 = (int64_t)ch * GR_CHUNK;
   const int64_t i1 = (i0 + GR_CHUNK) < N ? (i0 + GR_CHUNK) : N;
   double acc = 0.0;
@@ -194,10 +196,28 @@ __global__ void __launch_bounds__(256) grad_partial_kernel(const float2* __restr
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < 8; ++w) s += red[w];
-    if (nchunks == 1)
+    if (nchunks == 1 && out)
       out[j] = (float)s;
     else
       partial[j * nchunks + ch] = s;
+  }
+}
+
+// shared order: out[0] = the sum of all B * nchunks partials, one CTA in a fixed order
+// (thread t adds entries t, t + 1024, ...; then a fixed tree), so the result is
+// deterministic
+__global__ void __launch_bounds__(1024) grad_sum_kernel(const double* __restrict__ partial, int64_t count,
+                                                        float* __restrict__ out) {
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < count; t += blockDim.x) acc += partial[t];
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) out[0] = (float)acc;
   }
 }
 
@@ -350,16 +370,21 @@ cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* c
 int fg_grad_chunks(int64_t N) { return (int)((N + GR_CHUNK - 1) / GR_CHUNK); }
 
 cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N, float* out, double* partials,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool sum_all) {
   if (B <= 0) return cudaSuccess;
   const int nch = fg_grad_chunks(N);
-  if (B > 65535) return cudaErrorInvalidValue;
-  dim3 grid(nch, (unsigned)B);
+  if (B > 2147483647LL || nch > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)B, (unsigned)nch);
   FgTimed timed(FGFRFT_KC_GRAD_REDUCE, s);
-  fg_note_launch(FGFRFT_KC_GRAD_REDUCE, nch == 1 ? 1 : 2);
-  grad_partial_kernel<<<grid, 256, 0, s>>>(G, D, N, nch, partials, out);
+  fg_note_launch(FGFRFT_KC_GRAD_REDUCE, (nch == 1 && !sum_all) ? 1 : 2);
+  grad_partial_kernel<<<grid, 256, 0, s>>>(G, D, N, nch, partials, sum_all ? nullptr : out);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || nch == 1) return e;
+  if (e != cudaSuccess) return e;
+  if (sum_all) {
+    grad_sum_kernel<<<1, 1024, 0, s>>>(partials, B * nch, out);
+    return cudaGetLastError();
+  }
+  if (nch == 1) return cudaSuccess;
   grad_final_kernel<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(partials, nch, B, out);
   return cudaGetLastError();
 }

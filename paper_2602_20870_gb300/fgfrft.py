@@ -36,11 +36,11 @@ SIGNATURES = {
     "fgfrft_version": (_i32, []),
     "fgfrft_plan_bytes": (_sz, [_i64, _i32, _i32]),
     "fgfrft_precompute_work_bytes": (_sz, [_i64]),
-    "fgfrft_precompute": (_i32, [_vp, _i64, _i32, _i32, _vp, _i64, _vp, _sz, _vp, _sz, _vp,
+    "fgfrft_precompute": (_i32, [_vp, _i64, _i32, _i32, _vp, _i64, _dp, _vp, _vp, _sz, _vp, _sz, _vp,
                                  ctypes.POINTER(_vp)]),
     "fgfrft_plan_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                 ctypes.POINTER(_i32), ctypes.POINTER(_dp), ctypes.POINTER(_i32),
-                                ctypes.POINTER(_sz)]),
+                                ctypes.POINTER(_sz), ctypes.POINTER(_dp)]),
     "fgfrft_plan_block": (_vp, [_vp, _i32, _i32, ctypes.POINTER(_i64)]),
     "fgfrft_plan_status": (_i32, [_vp, _vp]),
     "fgfrft_plan_destroy": (_i32, [_vp]),
@@ -59,10 +59,44 @@ SIGNATURES = {
 NOALLOC_MAX_PARTIALS = 65536
 
 
+def _require(t, name: str, dtype, shape=None, min_numel=None):
+    """Raise ValueError unless ``t`` is a contiguous tensor of ``dtype`` (and, when given, of
+    ``shape``, with at least ``min_numel`` elements): the C calls take raw pointers and
+    sizes, so a mismatch here would be misread on the device."""
+    if not torch.is_tensor(t):
+        raise ValueError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name} has {t.numel()} elements, at least {min_numel} needed")
+
+
+def _require_cuda(tensors: dict, device=None):
+    """Raise ValueError unless every tensor is on one CUDA device (``device`` if given)."""
+    for name, t in tensors.items():
+        if t.device.type != "cuda":
+            raise ValueError(f"{name} must be on a CUDA device, not {t.device}")
+        want = device if device is not None else next(iter(tensors.values())).device
+        if t.device != want:
+            raise ValueError(f"{name} is on {t.device}, expected {want}")
+
+
 def grad_alpha_noalloc(G: torch.Tensor, D: torch.Tensor, out: torch.Tensor, stream=None):
     """Re <G_j, D_j> per signal row into ``out`` (float32, B) with no device allocation:
-    the library's fixed scratch holds the partial sums (see fgfrft_grad_alpha_noalloc)."""
+    the library's fixed scratch holds the partial sums (see fgfrft_grad_alpha_noalloc).
+    G and D: contiguous complex64 (B, N) on one CUDA device; out: contiguous float32 with
+    at least B elements on the same device."""
+    if not torch.is_tensor(G) or G.dim() != 2:
+        raise ValueError("G must be a (B, N) tensor")
     B, N = G.shape
+    _require(G, "G", torch.complex64)
+    _require(D, "D", torch.complex64, shape=(B, N))
+    _require(out, "out", torch.float32, min_numel=B)
+    _require_cuda({"G": G, "D": D, "out": out})
     rc = _lib().fgfrft_grad_alpha_noalloc(_ptr(G), _ptr(D), B, N, _ptr(out), ctypes.c_void_p(_stream(stream)))
     _check(rc, "fgfrft_grad_alpha_noalloc")
     return out
@@ -144,10 +178,15 @@ class Plan:
 
     ``F`` is an N x N unitary matrix (numpy or torch, converted to complex128 on
     the device).  The plan's device memory is a torch uint8 tensor owned here.
+    ``neg1_tol``: 0 classifies the lambda = -1 eigenvalues adaptively, a value in
+    [1e-6, 0.5] counts |lambda + 1| below it as -1 (see fgfrft_precompute).
+    ``keep_projector``: keep the FP64 projector (complex128 N x N, before rounding) in
+    ``self.P64``.  ``self.min_gap`` = (lower, upper) bound of min |lambda + 1| over
+    the complement.
     """
 
     def __init__(self, F, L_max: int, storage: int = STORE_C64 | STORE_SPLIT_F16 | STORE_ENTRY_F16, W=None,
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, neg1_tol: float = 0.0, keep_projector: bool = False):
         lib = _lib()
         Ft = torch.as_tensor(np.asarray(F) if not torch.is_tensor(F) else F)
         Ft = Ft.to(device=device, dtype=torch.complex128).contiguous()
@@ -167,19 +206,24 @@ class Plan:
             Wt = torch.as_tensor(np.asarray(W) if not torch.is_tensor(W) else W).to(
                 device=device, dtype=torch.complex128).contiguous()
             r = Wt.shape[1] if Wt.ndim == 2 else 0
+        self.P64 = torch.empty((N, N), dtype=torch.complex128, device=device) if keep_projector else None
         h = ctypes.c_void_p()
-        rc = lib.fgfrft_precompute(_ptr(Ft), N, L_max, storage, _ptr(Wt), r, _ptr(self.mem), nbytes,
-                                   _ptr(work), wbytes, ctypes.c_void_p(_stream(stream)), ctypes.byref(h))
+        rc = lib.fgfrft_precompute(_ptr(Ft), N, L_max, storage, _ptr(Wt), r, float(neg1_tol), _ptr(self.P64),
+                                   _ptr(self.mem), nbytes, _ptr(work), wbytes, ctypes.c_void_p(_stream(stream)),
+                                   ctypes.byref(h))
         _check(rc, "fgfrft_precompute")
         self._h = h
         del work
         n64, lm, st, rn, sq, pb = _i64(), _i32(), _i32(), _i32(), _i32(), _sz()
         res = _dp()
+        gap = (_dp * 2)()
         _check(lib.fgfrft_plan_info(h, ctypes.byref(n64), ctypes.byref(lm), ctypes.byref(st), ctypes.byref(rn),
-                                    ctypes.byref(res), ctypes.byref(sq), ctypes.byref(pb)), "fgfrft_plan_info")
+                                    ctypes.byref(res), ctypes.byref(sq), ctypes.byref(pb), gap), "fgfrft_plan_info")
         self.r_neg1, self.proj_residual, self.squarings, self.plan_bytes = rn.value, res.value, sq.value, pb.value
+        self.min_gap = (gap[0], gap[1])
         self.real = lib.fgfrft_plan_real(h) == 1
-        self._work = None
+        # one work buffer per CUDA stream: calls on different streams never share scratch
+        self._works = {}
 
     # ---------------------------------------------------------------- helpers
     @property
@@ -197,27 +241,45 @@ class Plan:
         except Exception:
             pass
 
-    def _with_work(self, op: int, alpha: np.ndarray, count: int, L: int, flags: int, call) -> int:
-        """call(w) -> status with the cached work buffer; the buffer is sized (a host pass over
-        the orders in fgfrft_work_bytes) only when there is none yet or the call reports it too
-        small, which it does before enqueuing anything."""
-        if self._work is not None:
-            rc = call(self._work)
+    def _stream_of(self, stream):
+        """(key, stream object) of the stream a call runs on; key 0 off CUDA (host tests)."""
+        if self.device.type != "cuda":
+            return 0, None
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return st.cuda_stream, st
+
+    def _with_work(self, op: int, alpha: np.ndarray, count: int, L: int, flags: int, call, stream=None) -> int:
+        """call(w) -> status with the stream's cached work buffer; the buffer is sized (a host
+        pass over the orders in fgfrft_work_bytes) only when the stream has none yet or the
+        call reports it too small, which it does before enqueuing anything."""
+        key, _ = self._stream_of(stream)
+        w = self._works.get(key)
+        if w is not None:
+            rc = call(w)
             if rc != ERR_INVALID_ARG:
                 return rc
             need = _lib().fgfrft_work_bytes(self._h, op, alpha.ctypes.data_as(ctypes.c_void_p), count, L, flags)
-            if need == 0 or need <= self._work.numel():
+            if need == 0 or need <= w.numel():
                 return rc  # an argument error, not the buffer size
-        return call(self.work_tensor(op, alpha, count, L, flags))
+        return call(self.work_tensor(op, alpha, count, L, flags, stream))
 
-    def work_tensor(self, op: int, alpha: np.ndarray, count: int, L: int, flags: int) -> torch.Tensor:
+    def work_tensor(self, op: int, alpha: np.ndarray, count: int, L: int, flags: int, stream=None) -> torch.Tensor:
+        """The work buffer of the stream (allocated on that stream, so the caching allocator
+        hands its memory to nothing else while the stream's kernels may still use it)."""
         n = _lib().fgfrft_work_bytes(self._h, op, alpha.ctypes.data_as(ctypes.c_void_p), count, L, flags)
         if n == 0:
             # invalid request: the call itself reports the precise status before using the buffer
             n = 256
-        if self._work is None or self._work.numel() < n:
-            self._work = torch.empty(n, dtype=torch.uint8, device=self.device)
-        return self._work
+        key, st = self._stream_of(stream)
+        w = self._works.get(key)
+        if w is None or w.numel() < n:
+            if st is not None:
+                with torch.cuda.stream(st):
+                    w = torch.empty(n, dtype=torch.uint8, device=self.device)
+            else:
+                w = torch.empty(n, dtype=torch.uint8, device=self.device)
+            self._works[key] = w
+        return w
 
     def block(self, l: int, storage: int = STORE_C64) -> torch.Tensor:
         """Stored block M_l (l in -L_max..L_max) or P (l = L_max + 1) as a device tensor view."""
@@ -263,7 +325,7 @@ class Plan:
             out = torch.empty((A, self.N, self.N), dtype=torch.complex64, device=self.device)
         rc = self._with_work(OP_ASSEMBLE, a, A, L, 0, lambda w: _lib().fgfrft_assemble(
             self._h, a.ctypes.data_as(ctypes.c_void_p), A, L, _ptr(out), _ptr(w), w.numel(),
-            ctypes.c_void_p(_stream(stream))))
+            ctypes.c_void_p(_stream(stream))), stream)
         _check(rc, "fgfrft_assemble")
         return out
 
@@ -288,7 +350,7 @@ class Plan:
         Y = torch.empty(Xd.shape, dtype=ydt, device=self.device) if (out is None or host) else out
         rc = self._with_work(OP_APPLY, a, B, L, flags, lambda w: _lib().fgfrft_apply(
             self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, _ptr(Xd), _ptr(Y), flags, _ptr(w), w.numel(),
-            ctypes.c_void_p(_stream(stream))))
+            ctypes.c_void_p(_stream(stream))), stream)
         _check(rc, "fgfrft_apply")
         if host:
             dst = out if out is not None else torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True)
@@ -300,6 +362,10 @@ class Plan:
         """(Y, dY/dalpha) from one pass over the stored powers (Prop. 3)."""
         L = self.L_max if L is None else int(L)
         X = X.contiguous()
+        if X.dim() != 2 or X.shape[1] != self.N:
+            raise ValueError(f"X must be (B, {self.N})")
+        _require(X, "X", torch.complex64)
+        _require_cuda({"X": X})
         B = X.shape[0]
         a = _alpha_array(alpha, B)
         flags = PATHS[path]
@@ -307,23 +373,33 @@ class Plan:
         D = torch.empty_like(X)
         rc = self._with_work(OP_GRAD, a, B, L, flags, lambda w: _lib().fgfrft_grad(
             self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, _ptr(X), _ptr(Y), _ptr(D), None, None, None, flags,
-            _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream))))
+            _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream))), stream)
         _check(rc, "fgfrft_grad(forward)")
         return Y, D
 
     def backward(self, alpha, G: torch.Tensor, D: torch.Tensor | None, L: int | None = None,
-                 need_x: bool = True, path: str = "auto", stream=None):
-        """(Q^H G, Re <G, D> per column) (Props. 2-3 and the chain rule)."""
+                 need_x: bool = True, path: str = "auto", stream=None, shared: bool = False):
+        """(Q^H G, Re <G, D> per column) (Props. 2-3 and the chain rule).  ``shared``: one
+        order for every column; the library then returns the one gradient of that order
+        (the sum over the columns) as a 1-element tensor."""
         L = self.L_max if L is None else int(L)
         G = G.contiguous()
+        if G.dim() != 2 or G.shape[1] != self.N:
+            raise ValueError(f"G must be (B, {self.N})")
         B = G.shape[0]
+        _require(G, "G", torch.complex64)
+        if D is not None:
+            _require(D, "D", torch.complex64, shape=(B, self.N))
+        _require_cuda({"G": G, "D": D} if D is not None else {"G": G})
         a = _alpha_array(alpha, B)
-        flags = PATHS[path]
+        if shared:
+            a = a[:1]
+        flags = PATHS[path] | (SHARED_ALPHA if shared else 0)
         gX = torch.empty_like(G) if need_x else None
-        ga = torch.empty(B, dtype=torch.float32, device=G.device) if D is not None else None
+        ga = torch.empty(1 if shared else B, dtype=torch.float32, device=G.device) if D is not None else None
         rc = self._with_work(OP_GRAD, a, B, L, flags, lambda w: _lib().fgfrft_grad(
             self._h, a.ctypes.data_as(ctypes.c_void_p), B, L, None, None, _ptr(D), _ptr(G), _ptr(gX), _ptr(ga),
-            flags, _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream))))
+            flags, _ptr(w), w.numel(), ctypes.c_void_p(_stream(stream))), stream)
         _check(rc, "fgfrft_grad(backward)")
         return gX, ga
 
@@ -389,6 +465,7 @@ class FGFRFTFunction(torch.autograd.Function):
         ctx.plan, ctx.L, ctx.path, ctx.a = plan, L, path, a
         ctx.alpha_device, ctx.alpha_dtype = alpha.device, alpha.dtype
         ctx.shared = alpha.numel() == 1 and B > 1
+        ctx.alpha_shape = alpha.shape
         ctx.save_for_backward(D)
         return Y
 
@@ -396,12 +473,12 @@ class FGFRFTFunction(torch.autograd.Function):
     def backward(ctx, G):
         (D,) = ctx.saved_tensors
         need_x = ctx.needs_input_grad[1]
-        gX, ga = ctx.plan.backward(ctx.a, G.to(torch.complex64), D, ctx.L, need_x, ctx.path)
+        # a shared order: the library sums the per-column gradients into one value
+        gX, ga = ctx.plan.backward(ctx.a, G.to(torch.complex64).contiguous(), D, ctx.L, need_x, ctx.path,
+                                   shared=ctx.shared)
         galpha = None
         if ctx.needs_input_grad[0]:
-            galpha = ga.to(device=ctx.alpha_device, dtype=ctx.alpha_dtype)
-            if ctx.shared:
-                galpha = galpha.sum().reshape(1)
+            galpha = ga.to(device=ctx.alpha_device, dtype=ctx.alpha_dtype).reshape(ctx.alpha_shape)
         return galpha, gX, None, None, None
 
 

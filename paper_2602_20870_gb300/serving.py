@@ -64,6 +64,7 @@ class _Pending:
     fut: Future
     arrival: float
     nbytes: int
+    x: np.ndarray | None = None  # the request's signals as complex64 (cols, N), set at submit
 
 
 @dataclass
@@ -77,6 +78,7 @@ class _Batch:
     nbytes: int
     deadline: float
     launched: float = 0.0
+    slot: int = -1  # the graph's pinned staging slot this batch's signals went through
 
 
 def ncols(req) -> int:
@@ -112,6 +114,11 @@ class Server:
         self.t0 = time.perf_counter()
         self.launches = 0
         self.max_reserved = 0
+        # per graph: max_inflight pinned host slots of max_cols signals each; a batch's
+        # signals are gathered into a free slot and reach the device in one copy, and the
+        # slot is free again once the batch's event has completed
+        self.slots = [None] * len(self.graphs)
+        self.slot_busy = [[False] * max_inflight_per_graph for _ in self.graphs]
 
     # ------------------------------------------------------------------ client side
     def now(self) -> float:
@@ -128,6 +135,12 @@ class Server:
         if p.nbytes > self.budget:
             p.fut.set_exception(MemoryError("request larger than the HBM budget"))
             return p.fut
+        if ncols(req) > self.max_cols:
+            p.fut.set_exception(ValueError("request has more signals than a batch holds"))
+            return p.fut
+        if req.kind != "assemble":
+            # converted once here, by the submitting thread, not on the scheduler's launch path
+            p.x = np.ascontiguousarray(np.asarray(req.X).reshape(-1, N), dtype=np.complex64)
         with self.lock:
             self.pending.append(p)
         return p.fut
@@ -148,6 +161,8 @@ class Server:
         for b in done:
             self.inflight.remove(b)
             self.reserved -= b.nbytes
+            if b.slot >= 0:
+                self.slot_busy[b.graph][b.slot] = False
             t = self.now()
             for it, out in zip(b.items, b.outputs["per_item"]):
                 it.fut.set_result(Result(it.req.rid, b.kind, out[0], out[1], it.arrival, t))
@@ -190,19 +205,38 @@ class Server:
         self.max_reserved = max(self.max_reserved, self.reserved)
         return launched
 
+    def _stage(self, g: int, items: list):
+        """Gather the items' signals into a free pinned slot of graph g: (slot, pinned rows)."""
+        N = self.graphs[g].plan.N
+        if self.slots[g] is None:
+            self.slots[g] = [torch.empty((self.max_cols, N), dtype=torch.complex64, pin_memory=True)
+                             for _ in range(self.max_inflight)]
+        slot = self.slot_busy[g].index(False)  # admission keeps at most max_inflight batches per graph
+        self.slot_busy[g][slot] = True
+        buf = self.slots[g][slot]
+        view = buf.numpy()
+        off = 0
+        for it in items:
+            c = it.x.shape[0]
+            view[off:off + c] = it.x
+            off += c
+        return slot, buf[:off]
+
     def _launch(self, g: int, kind: str, L: int, items: list):
         graph = self.graphs[g]
         plan, stream = graph.plan, graph.stream
         nbytes = sum(it.nbytes for it in items)
         per_item = []
+        slot = -1
         with torch.cuda.stream(stream):
             if kind == "assemble":
                 alphas = np.array([float(it.req.alpha[0]) for it in items])
                 Q = plan.assemble(alphas, L, stream=stream)
                 per_item = [(Q[i:i + 1], None) for i in range(len(items))]
             else:
-                X = torch.cat([torch.as_tensor(it.req.X, dtype=torch.complex64).pin_memory()
-                               .to("cuda", non_blocking=True) for it in items], 0)
+                slot, host = self._stage(g, items)
+                X = torch.empty(host.shape, dtype=torch.complex64, device=plan.device)
+                X.copy_(host, non_blocking=True)
                 alphas = np.concatenate([np.asarray(it.req.alpha, dtype=np.float64) for it in items])
                 if kind == "apply":
                     path = self.path if self.path != "auto" else "stacked"
@@ -222,7 +256,7 @@ class Server:
             ev.record(stream)
         self.launches += 1
         self.inflight.append(_Batch(g, kind, L, items, ev, {"per_item": per_item}, nbytes,
-                                    self.now() + self.deadline_s, self.now()))
+                                    self.now() + self.deadline_s, self.now(), slot))
 
     def step(self) -> bool:
         """One scheduler tick; returns True if anything happened."""

@@ -106,6 +106,14 @@ def prescribed_spectrum_unitary(n: int, r_neg1: int, seed: int, margin: float = 
     return (V * lam[None, :]) @ V.conj().T
 
 
+def unitary_with_phases(theta, seed: int) -> np.ndarray:
+    """V diag(e^{j theta_k}) V^H for the given eigenphases, V Haar-like: a test unitary
+    whose distances |lambda_k + 1| = 2 |cos(theta_k / 2)| are known exactly."""
+    th = np.asarray(theta, dtype=np.float64)
+    V = random_unitary(th.size, seed)
+    return (V * np.exp(1j * th)[None, :]) @ V.conj().T
+
+
 # ----------------------------------------------------------------------------
 # signals
 # ----------------------------------------------------------------------------

@@ -77,8 +77,42 @@ def test_host_argument_checks_without_gpu(lib):
     from paper_2602_20870_gb300 import fgfrft as FG
     L = FG.load()
     h = ctypes.c_void_p()
-    assert L.fgfrft_precompute(None, 64, 4, 1, None, 0, None, 0, None, 0, None, ctypes.byref(h)) == FG.ERR_INVALID_ARG
+    assert L.fgfrft_precompute(None, 64, 4, 1, None, 0, 0.0, None, None, 0, None, 0, None,
+                               ctypes.byref(h)) == FG.ERR_INVALID_ARG
+    # neg1_tol outside {0} U [1e-6, 0.5] is refused before anything else is looked at
+    buf = ctypes.create_string_buffer(1 << 16)
+    base = (ctypes.addressof(buf) + 255) // 256 * 256
+    for tol in (-1.0, 1e-7, 0.6, float("nan")):
+        assert L.fgfrft_precompute(ctypes.c_void_p(base), 4, 1, 1, None, 0, tol, None, ctypes.c_void_p(base),
+                                   1 << 12, ctypes.c_void_p(base), 1 << 12, None, ctypes.byref(h)) == FG.ERR_INVALID_ARG
+    # plan_info on no plan
+    assert L.fgfrft_plan_info(None, None, None, None, None, None, None, None, None) == FG.ERR_INVALID_ARG
     assert L.fgfrft_apply(None, None, 1, 0, None, None, 0, None, 0, None) == FG.ERR_INVALID_ARG
     assert L.fgfrft_grad(None, None, 1, 0, None, None, None, None, None, None, 0, None, 0, None) == FG.ERR_INVALID_ARG
     assert L.fgfrft_assemble(None, None, 1, 0, None, None, 0, None) == FG.ERR_INVALID_ARG
     assert L.fgfrft_plan_destroy(None) == FG.ERR_INVALID_ARG
+
+
+def test_binding_rejects_mismatched_tensors_before_the_call():
+    """The binding checks dtype, contiguity, shape, size and device of the tensors it
+    passes as raw pointers (a short or misread buffer would be accessed on the GPU)."""
+    import pytest
+    import torch
+    from paper_2602_20870_gb300 import fgfrft as FG
+    G = torch.zeros((3, 8), dtype=torch.complex64)
+    D = torch.zeros((3, 8), dtype=torch.complex64)
+    out = torch.zeros(3, dtype=torch.float32)
+    cases = [
+        (G.to(torch.complex128), D, out, "G must be torch.complex64"),
+        (G, D.to(torch.complex128), out, "D must be torch.complex64"),
+        (G, torch.zeros((3, 16), dtype=torch.complex64)[:, ::2], out, "D must be contiguous"),
+        (G, torch.zeros((4, 8), dtype=torch.complex64), out, "D has shape"),
+        (G, D, torch.zeros(2, dtype=torch.float32), "out has 2 elements"),
+        (G, D, out.to(torch.float64), "out must be torch.float32"),
+        (G, D, out, "G must be on a CUDA device"),
+    ]
+    for g, d, o, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            FG.grad_alpha_noalloc(g, d, o)
+    with pytest.raises(ValueError, match="must be a"):
+        FG.grad_alpha_noalloc(G[0], D, out)

@@ -285,6 +285,63 @@ def test_frobenius_identity_and_bounds():
             prev = err
 
 
+def test_pointwise_bound_is_tight_to_its_asymptotic_constant():
+    """Thm. 1 from both sides.  Each tail of R_L(theta) = sum_{|n|>L} c_n e^{jn theta} is an
+    alternating-sign series with terms sin(pi a)/(pi (a - n)); summed in closed form its
+    modulus is asymptotically |sin(pi a)| / (pi L |1 + e^{j theta}|) = |sin(pi a)| /
+    (2 pi L cos(theta/2)), and the two tails rotate as e^{+-j(L+1) theta}.  Their moduli add
+    somewhere in every theta window of width pi/(L+1), where |R_L| reaches half of the
+    bound |sin(pi a)|/(pi cos(theta/2)) (1/(L+1-a) + 1/(L+1+a)) ~ 2|sin(pi a)|/(pi L
+    cos(theta/2)).  So the windowed maximum of |R_L| / bound lies just above 1/2: a bound
+    with a wrong cosine argument or an extra factor fails one side."""
+    for a in [0.5, 0.37, -1.3, 1.9]:
+        for L in [10, 30, 60]:
+            for t0 in [0.5, 1.5, 2.5, -2.0]:
+                th = np.linspace(t0, t0 + math.pi / (L + 1), 400)
+                ratio = np.abs(O.trunc_error(th, a, L)) / O.pointwise_bound(th, a, L)
+                assert ratio.max() <= 1.0
+                assert 0.5 <= ratio.max() <= 0.5 + 0.25 / L, (a, L, t0, ratio.max())
+
+
+def test_bound_values_by_hand_and_between_the_two_theorems():
+    """Hand values: at theta = 0, a = 1/2, L = 1 the Thm. 1 bound is (1/pi)(1/1.5 + 1/2.5);
+    at theta = 2 pi/3 (cos(theta/2) = 1/2) twice that.  For F = j I_4 (every theta = pi/2,
+    cos(theta/2) = 1/sqrt 2) Thm. 2's two bounds coincide and equal
+    2 (L+1) |sin(pi a)| sqrt(N) / (pi cos (L+1)^2 - a^2)) = 8 sqrt 2 / (3.75 pi).
+    Across the theorems: the tight Frobenius bound is the root sum of squares of the
+    pointwise bounds over the complement (the per-eigenvalue form of Thm. 2)."""
+    b = O.pointwise_bound(np.array([0.0, 2 * math.pi / 3]), 0.5, 1)
+    v = (1 / 1.5 + 1 / 2.5) / math.pi
+    assert abs(b[0] - v) < 1e-15 and abs(b[1] - 2 * v) < 1e-15
+    sp = O.spectral(1j * np.eye(4))
+    want = 8 * math.sqrt(2) / (3.75 * math.pi)
+    assert abs(O.frobenius_bound_tight(sp, 0.5, 1) - want) < 1e-14
+    assert abs(O.frobenius_bound_simplified(sp, 0.5, 1) - want) < 1e-14
+    for F in [W.random_unitary(60, 3), W.prescribed_spectrum_unitary(50, 2, 9), W.tiny().F]:
+        sp = O.spectral(F)
+        comp = ~sp.neg1
+        for a, L in [(0.37, 8), (-1.3, 20), (1.9, 40)]:
+            rss = math.sqrt(np.sum(O.pointwise_bound(sp.theta[comp], a, L) ** 2))
+            assert abs(O.frobenius_bound_tight(sp, a, L) - rss) < 1e-12 * rss
+            # and the simplified bound replaces every cosine by the smallest one
+            n = int(comp.sum())
+            worst = O.pointwise_bound(np.array([2 * math.acos(sp.cos_c_min)]), a, L)[0]
+            assert abs(O.frobenius_bound_simplified(sp, a, L) - math.sqrt(n) * worst) < 1e-12 * worst * n
+
+
+def test_bound_pins_catch_planted_mistakes(monkeypatch):
+    """cos(theta) for cos(theta/2), or a bound loosened by a constant, fails the pins above."""
+    real = O.pointwise_bound
+    L, a = 30, 0.37
+    th = np.linspace(2.5, 2.5 + math.pi / (L + 1), 400)
+    for bad in (lambda t, al, LL: real(2 * np.asarray(t), al, LL),
+                lambda t, al, LL: 2.0 * real(t, al, LL)):
+        monkeypatch.setattr(O, "pointwise_bound", bad)
+        r = np.abs(O.trunc_error(th, a, L)) / O.pointwise_bound(th, a, L)
+        assert not (r.max() <= 1.0 and 0.5 <= r.max() <= 0.5 + 0.25 / L)
+    monkeypatch.undo()
+
+
 def test_unitarity_reconstruction_additivity_bounds():
     """Props. 4-6: ||Q^H Q - I|| <= 2e + e^2; ||x^ - x|| <= (2e + e^2)||x||; additivity defect."""
     F = W.random_unitary(120, 8)
