@@ -155,16 +155,23 @@ size_t fgfrft_precompute_work_bytes(int64_t N);
  *               theta_k = pi}; the paper fixes no tolerance for it).
  *   r_W         number of columns of W_dev (ignored when W_dev is NULL).
  *   neg1_tol    which eigenvalues count as -1 when W_dev is NULL:
- *               0: adaptive.  S is squared until its powers separate into the
- *                  two basins of McWeeny's iteration (at most 2^46-th power), so
- *                  the widest gap in |lambda + 1| below that scale decides.  The
- *                  call then refuses (FGFRFT_ERR_AMBIGUOUS_SPECTRUM) a spectrum
- *                  with an eigenvalue in the band FP64 cannot certify: one left in
- *                  the complement closer than 1e-6 to -1 (min_gap below), or one
- *                  counted as -1 whose |lambda + 1| exceeds the rounding level of
- *                  P (max(1e-9, 256 u N / min_gap), u = 2^-53, and at most 1e-6),
- *                  measured by proj_residual / sqrt(r_neg1).
- *               in [1e-6, 0.5]: fixed threshold.  S is squared exactly
+ *               0: adaptive, with the oracle's classification (|lambda + 1| <=
+ *                  1e-8 is -1) wherever FP64 can certify it.  S is squared until
+ *                  its powers separate into the two basins of McWeeny's iteration,
+ *                  so the widest gap in |lambda + 1| decides; while the counted set
+ *                  holds eigenvalues that are not -1 to FP64 accuracy (its residual
+ *                  ||F P + P|| / sqrt(r_neg1) above max(1e-10, 64 u N / min_gap),
+ *                  u = 2^-53, at most 1e-6), P S P is squared again until some of
+ *                  them decay, and those move to the complement (at most three
+ *                  rounds).  Squarings stop at 2^m with m <= log2(0.02 / (u sqrt N))
+ *                  (40 to 44 for N = 16384 .. 64), where FP64 drift of an exact -1
+ *                  eigenvalue would become visible.  The call refuses
+ *                  (FGFRFT_ERR_AMBIGUOUS_SPECTRUM) a spectrum it cannot certify: an
+ *                  eigenvalue left in the complement closer than 1e-6 to -1
+ *                  (min_gap below), or a counted set that cannot be separated
+ *                  within the squaring limit (|lambda + 1| between about 1e-10 and
+ *                  2e-6).
+ *               in [1e-5, 0.5]: fixed threshold.  S is squared exactly
  *                  ceil(log2(4 ln 2 / neg1_tol^2)) times, which takes an eigenvalue
  *                  with |lambda + 1| = neg1_tol to at most 1/2; eigenvalues below
  *                  about 0.28 x that boundary count as -1, those above about 2.06 x

@@ -149,10 +149,11 @@ constexpr int kAssembledMinRun = 64;
 
 // Classification of the lambda = -1 eigenvalues (offline projector).
 constexpr int kMaxSquarings = 46;           // adaptive route: at most 2^46-th power of S
-constexpr double kNeg1TolMin = 1e-6;        // fixed threshold: FP64 resolves 1 - g^2/4 down to here
+constexpr double kNeg1TolMin = 1e-5;        // fixed threshold: FP64 resolves 1 - g^2/4 down to here
 constexpr double kNeg1TolMax = 0.5;
 constexpr double kAmbiguousGap = 1e-6;      // adaptive route: complement eigenvalues closer to -1 are refused
-constexpr double kResidualFloor = 1e-9;     // adaptive route: |lambda + 1| of the counted eigenvalues below this
+constexpr double kResidualFloor = 1e-10;    // adaptive route: |lambda + 1| of the counted eigenvalues below this
+constexpr int kRefineRounds = 3;            // adaptive route: separations of the counted set
 constexpr double kGapBracket = 1.01;        // min_gap bracket: upper / lower bound at most this
 constexpr int kMaxGapPower = 52;            // ... or the bracket of S^(2^52), whichever comes first
 
@@ -267,6 +268,17 @@ cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const do
                            w.coef + a * (2 * L + 2), Qc ? Qc + a * p->N * p->N : nullptr,
                            Qs ? Qs + a * 4 * p->qplane : nullptr, p->qplane,
                            !(p->real && p->r_neg1 == 0), p->dstatus, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  if (!p->c64 && p->real && p->f16) {  // real split planes only: per order, the two real planes
+    cudaError_t e = fg_coeffs(alpha_dev, (int)A, L, false, w.coef, nullptr, 1, 2 * L + 2, s);
+    if (e != cudaSuccess) return e;
+    for (int64_t a = 0; a < A; ++a) {
+      e = fg_assemble_single_real(p->f16, 4 * p->plane_elems, p->plane_elems, b0, nb, pb, p->N, p->Np,
+                                  w.coef + a * (2 * L + 2), Qc ? Qc + a * p->N * p->N : nullptr,
+                                  Qs ? Qs + a * 4 * p->qplane : nullptr, p->qplane, p->r_neg1 > 0, p->dstatus, s);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -500,10 +512,118 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
     return fg_zgemm(ta, tb, n, n, n, alpha, A, n, B, n, zero, C, n, s, rg);
   };
 
-  // (2) projector P onto the lambda = -1 eigenspace, into Cm.  The route without W leaves
-  // S^(2^squarings) in Dm for the gap estimate below.
+  // (2) projector P onto the lambda = -1 eigenspace, into Cm.
+  //
+  // S = T T^H with T = (I - F)/2 has eigenvalues s_k = 1 - |lambda_k + 1|^2 / 4, exactly 1 on
+  // the -1 eigenspace.  After m squarings they are s_k^(2^m) ~ exp(-2^m |lambda_k + 1|^2 / 4).
+  // separate(H): square the Hermitian H (in Bm) until every eigenvalue lies in one of the two
+  // basins of McWeeny's iteration -- tr(H) - ||H||_F^2 = sum h_k (1 - h_k) < 0.05 puts each
+  // below 0.053 or above 0.947 -- or, with a fixed count, exactly that many times and then
+  // require the same; purify P <- 3P^2 - 2P^3 into Cm and leave H^(2^m) in Dm.
+  auto form_S = [&](double2* dst) -> bool {  // dst = S (uses Am)
+    return fg_zaxpby_identity(N, make_double2(-0.5, 0.0), (const double2*)F_dev, zero, make_double2(0.5, 0.0), Am,
+                              s) == cudaSuccess &&
+           gemm(false, true, one, Am, Am, dst) == cudaSuccess;
+  };
+  // FP64 rounding moves an eigenvalue that is exactly 1 by about u sqrt(N) per squaring, and
+  // 2^m squarings compound it: at most max_sq(N) squarings keep that drift below 0.02.
+  const int max_sq =
+      std::max(1, std::min(kMaxSquarings, (int)floor(log2(0.02 / (1.1102230246251565e-16 * sqrt((double)N))))));
+  int sq_used = 0;
+  // drop >= 0: a refinement of a counted set of rank drop; the trace of the powers must first
+  // fall below drop - 1/2 (some counted eigenvalue has decayed) before separation counts
+  auto separate = [&](int fixed, int drop) -> int {
+    double2* cur = Bm;
+    double2* tmp = Am;
+    bool converged = false;
+    const int limit = fixed ? fixed : max_sq;
+    int m = 1;
+    for (; m <= limit; ++m) {
+      if (gemm(false, false, one, cur, cur, tmp) || fg_zherm_sym(N, tmp, s)) return FGFRFT_ERR_CUDA;
+      std::swap(cur, tmp);
+      if (fg_ztrace_fro(N, cur, nullptr, red, s) || !readback()) return FGFRFT_ERR_CUDA;
+      if (fixed && m < fixed) continue;
+      if (drop >= 0 && h[0] > drop - 0.5) continue;
+      if (h[0] - h[1] < 0.05) {
+        converged = true;
+        break;
+      }
+    }
+    if (!converged) return FGFRFT_ERR_AMBIGUOUS_SPECTRUM;
+    sq_used = m;
+    if (cudaMemcpyAsync(Dm, cur, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return FGFRFT_ERR_CUDA;
+    for (int it = 0; it < 12; ++it) {
+      if (gemm(false, false, one, cur, cur, tmp) ||          // P^2
+          gemm(false, false, one, tmp, cur, Cm) ||           // P^3
+          fg_ztrace_fro(N, tmp, cur, red, s) || !readback())  // ||P^2 - P||
+        return FGFRFT_ERR_CUDA;
+      if (fg_zmcweeny(N, tmp, Cm, cur, s) || fg_zherm_sym(N, cur, s)) return FGFRFT_ERR_CUDA;
+      if (sqrt(h[1]) < 1e-13 * sqrt((double)N)) break;
+    }
+    if (cudaMemcpyAsync(Cm, cur, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return FGFRFT_ERR_CUDA;
+    return FGFRFT_OK;
+  };
+  // rank of P = round(tr P) (P = 0 when it rounds to 0), and the residual ||F P + P||_F
+  // (= sqrt(sum over the counted eigenvalues of |lambda + 1|^2) for the exact projector)
+  int rank = 0;
+  double residual = 0.0;
+  auto rank_and_residual = [&]() -> int {
+    if (fg_ztrace_fro(N, Cm, nullptr, red, s) || !readback()) return FGFRFT_ERR_CUDA;
+    rank = (int)llround(h[0]);
+    if (rank < 0 || fabs(h[0] - rank) > 1e-6) return FGFRFT_ERR_AMBIGUOUS_SPECTRUM;
+    if (rank == 0 && cudaMemsetAsync(Cm, 0, (size_t)N * N * sizeof(double2), s) != cudaSuccess)
+      return FGFRFT_ERR_CUDA;
+    if (gemm(false, false, one, (const double2*)F_dev, Cm, Am) || fg_zaxpby_identity(N, one, Cm, one, zero, Am, s) ||
+        fg_ztrace_fro(N, Am, nullptr, red, s) || !readback())
+      return FGFRFT_ERR_CUDA;
+    residual = sqrt(h[1]);
+    return FGFRFT_OK;
+  };
+  // Bracket of the largest eigenvalue below 1 of H^(2^m0) - P (held in Dm; Bm is scratch), as
+  // a bracket of the smallest |lambda + 1| among the eigenvalues it holds: with mu_k the
+  // eigenvalues of (H^(2^m0) - P)^(2^j) and x = 2^(m0 + j),
+  // (sum mu^2 / sum mu)^(1/x) <= s_max <= (sum mu)^(1/x), s_max = 1 - g^2 / 4; squared
+  // (normalised, its scale kept as a logarithm) until upper / lower <= kGapBracket.
+  double gap_lo = INFINITY, gap_hi = INFINITY;
+  auto bracket = [&](int m0) -> int {
+    if (fg_zaxpby_identity(N, make_double2(-1.0, 0.0), Cm, one, zero, Dm, s)) return FGFRFT_ERR_CUDA;
+    double2* T = Dm;
+    double2* T2 = Bm;
+    double lnc = 0.0;
+    double glo = 0.0, ghi = 2.0;
+    for (int j = 0;; ++j) {
+      if (fg_ztrace_fro(N, T, nullptr, red, s) || !readback()) return FGFRFT_ERR_CUDA;
+      const double A = h[0], Bq = h[1];
+      const double x = ldexp(1.0, m0 + j);
+      if (!(A > 1e-300) || !(Bq > 0.0)) {  // the powers vanish: every s_k below the bound
+        const double ln_hi = (lnc + log(1e-300)) / x;
+        glo = ln_hi < 0.0 ? 2.0 * sqrt(-expm1(ln_hi)) : 0.0;
+        ghi = 2.0;
+        break;
+      }
+      const double ln_hi = (lnc + log(A)) / x;            // log of the upper bound of s_max
+      const double ln_lo = (lnc + log(Bq) - log(A)) / x;  // log of the lower bound
+      glo = ln_hi < 0.0 ? 2.0 * sqrt(-expm1(ln_hi)) : 0.0;
+      ghi = ln_lo < 0.0 ? 2.0 * sqrt(-expm1(ln_lo)) : 0.0;
+      if ((glo > 0.0 && ghi <= kGapBracket * glo) || m0 + j >= kMaxGapPower) break;
+      // T <- T^2 / ||T||_F^2 (trace 1 for a Hermitian T), c <- c^2 ||T||_F^2
+      if (gemm(false, false, make_double2(1.0 / Bq, 0.0), T, T, T2) || fg_zherm_sym(N, T2, s)) return FGFRFT_ERR_CUDA;
+      std::swap(T, T2);
+      lnc = 2.0 * lnc + log(Bq);
+    }
+    if (glo < gap_lo) {
+      gap_lo = glo;
+      gap_hi = std::max(glo, ghi);
+    }
+    return FGFRFT_OK;
+  };
+  const double u = 1.1102230246251565e-16;
   int squarings = 0;
+  int rc = FGFRFT_OK;
   if (W_dev) {
+    // the caller's eigenspace: P = W W^H; the complement's gap from S - P
     if (r_W > 0) {
       if (fg_zgemm(false, true, n, n, (int)r_W, one, (const double2*)W_dev, (int)r_W, (const double2*)W_dev,
                    (int)r_W, zero, Cm, n, s))
@@ -511,121 +631,57 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
     } else if (cudaMemsetAsync(Cm, 0, (size_t)N * N * sizeof(double2), s) != cudaSuccess) {
       return fail(FGFRFT_ERR_CUDA);
     }
+    if ((rc = rank_and_residual())) return fail(rc);
+    if (rank < N) {
+      if (!form_S(Dm)) return fail(FGFRFT_ERR_CUDA);
+      if ((rc = bracket(0))) return fail(rc);
+    }
+    if (rank > 0 && !(residual <= 1e-6 * sqrt((double)rank))) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
+  } else if (neg1_tol > 0.0) {
+    // fixed threshold: the squaring count sets the boundary at neg1_tol (its guard band is the
+    // separation test); the complement's gap from S - P
+    if (!form_S(Bm)) return fail(FGFRFT_ERR_CUDA);
+    if ((rc = separate(squarings_for_tol(neg1_tol), -1))) return fail(rc);
+    squarings = sq_used;
+    if ((rc = rank_and_residual())) return fail(rc);
+    if (rank < N) {
+      if (!form_S(Dm)) return fail(FGFRFT_ERR_CUDA);
+      if ((rc = bracket(0))) return fail(rc);
+    }
+    // the counted eigenvalues lie below ~0.3 neg1_tol
+    if (rank > 0 && !(residual <= neg1_tol * sqrt((double)rank))) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
   } else {
-    // T = (I - F)/2 -> Am;  S = T T^H -> Bm  (eigenvalues s_k = sin^2(theta_k/2) = 1 - |lambda_k + 1|^2 / 4)
-    if (fg_zaxpby_identity(N, make_double2(-0.5, 0.0), (const double2*)F_dev, zero, make_double2(0.5, 0.0), Am, s) ||
-        gemm(false, true, one, Am, Am, Bm))
-      return fail(FGFRFT_ERR_CUDA);
-    double2* cur = Bm;
-    double2* tmp = Am;
-    bool converged = false;
-    // After m squarings the eigenvalues are s_k^(2^m) ~ exp(-2^m |lambda_k + 1|^2 / 4).
-    // Adaptive (neg1_tol = 0): square until every eigenvalue is within the basin of McWeeny
-    // purification: tr(S) - ||S||_F^2 = sum s_k (1 - s_k) < 0.05 puts each s_k below 0.053
-    // or above 0.947.  Fixed threshold: square exactly the number of times that takes an
-    // eigenvalue with |lambda + 1| = neg1_tol to at most 1/2 (McWeeny's dividing point),
-    // then require the same separation.
-    const int fixed = neg1_tol > 0.0 ? squarings_for_tol(neg1_tol) : 0;
-    const int max_sq = fixed ? fixed : kMaxSquarings;
-    for (squarings = 1; squarings <= max_sq; ++squarings) {
-      if (gemm(false, false, one, cur, cur, tmp) || fg_zherm_sym(N, tmp, s)) return fail(FGFRFT_ERR_CUDA);
-      std::swap(cur, tmp);
-      if (fg_ztrace_fro(N, cur, nullptr, red, s) || !readback()) return fail(FGFRFT_ERR_CUDA);
-      if (fixed && squarings < fixed) continue;
-      if (h[0] - h[1] < 0.05) {
-        converged = true;
-        break;
+    // adaptive: separate S at its widest gap; while the counted set holds eigenvalues that
+    // are not -1 to FP64 accuracy (residual above the rounding level of P, which grows as
+    // u N / gap), separate P S P again within it.  The eigenvalues each round removes join
+    // the complement, whose gap is bracketed from the round's last power.
+    if (!form_S(Bm)) return fail(FGFRFT_ERR_CUDA);
+    bool accepted = false;
+    for (int round = 0; round < kRefineRounds && !accepted; ++round) {
+      const int prev_rank = rank;
+      if ((rc = separate(0, round > 0 ? prev_rank : -1))) return fail(rc);
+      squarings += sq_used;
+      if ((rc = rank_and_residual())) return fail(rc);
+      if (round > 0 && rank >= prev_rank) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);  // no progress
+      if (rank < N && (rc = bracket(sq_used))) return fail(rc);
+      const double thr = std::min(1e-6, std::max(kResidualFloor, 64.0 * u * (double)N / std::max(gap_lo, 1e-300)));
+      accepted = rank == 0 || residual <= thr * sqrt((double)rank);
+      if (!accepted) {
+        // H = P S P: the counted eigenvalues' s_k, zero elsewhere
+        if (!form_S(Bm) || gemm(false, false, one, Cm, Bm, Dm) || gemm(false, false, one, Dm, Cm, Bm) ||
+            fg_zherm_sym(N, Bm, s))
+          return fail(FGFRFT_ERR_CUDA);
       }
     }
-    if (!converged) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
-    if (cudaMemcpyAsync(Dm, cur, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return fail(FGFRFT_ERR_CUDA);
-    // McWeeny purification P <- 3 P^2 - 2 P^3 (quadratic convergence to 0 / 1)
-    for (int it = 0; it < 12; ++it) {
-      if (gemm(false, false, one, cur, cur, tmp) ||          // P^2
-          gemm(false, false, one, tmp, cur, Cm) ||           // P^3
-          fg_ztrace_fro(N, tmp, cur, red, s) || !readback())  // ||P^2 - P||
-        return fail(FGFRFT_ERR_CUDA);
-      if (fg_zmcweeny(N, tmp, Cm, cur, s) || fg_zherm_sym(N, cur, s)) return fail(FGFRFT_ERR_CUDA);
-      if (sqrt(h[1]) < 1e-13 * sqrt((double)N)) break;
-    }
-    if (cudaMemcpyAsync(Cm, cur, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return fail(FGFRFT_ERR_CUDA);
+    if (!accepted) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
+    if (rank < N && gap_lo < kAmbiguousGap) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
   }
-  if (fg_ztrace_fro(N, Cm, nullptr, red, s) || !readback()) return fail(FGFRFT_ERR_CUDA);
-  p->r_neg1 = (int)llround(h[0]);
-  if (p->r_neg1 < 0 || fabs(h[0] - p->r_neg1) > 1e-6) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
-  if (p->r_neg1 == 0 && cudaMemsetAsync(Cm, 0, (size_t)N * N * sizeof(double2), s) != cudaSuccess)
-    return fail(FGFRFT_ERR_CUDA);
+  p->r_neg1 = rank;
+  p->proj_residual = residual;
   p->squarings = squarings;
-  // residual ||F P + P||_F = sqrt(sum_{k in I} |lambda_k + 1|^2) for the exact projector
-  if (gemm(false, false, one, (const double2*)F_dev, Cm, Am) || fg_zaxpby_identity(N, one, Cm, one, zero, Am, s) ||
-      fg_ztrace_fro(N, Am, nullptr, red, s) || !readback())
-    return fail(FGFRFT_ERR_CUDA);
-  p->proj_residual = sqrt(h[1]);
-
-  // (2b) the gap of the complement, min_{k not in I} |lambda_k + 1|, bracketed from the
-  // traces of repeated squares of T = S^(2^m) - P (the complement part of S^(2^m); m = 0 and
-  // S = (I - F)(I - F)^H / 4 when W was given).  With mu_k the eigenvalues of T^(2^j) and
-  // x = 2^(m + j): (sum mu^2 / sum mu)^(1/x) <= s_max <= (sum mu)^(1/x), s_max = 1 - g^2/4.
-  if (p->r_neg1 >= N) {
-    p->min_gap_lo = p->min_gap_hi = INFINITY;
-  } else {
-    if (W_dev) {
-      if (fg_zaxpby_identity(N, make_double2(-0.5, 0.0), (const double2*)F_dev, zero, make_double2(0.5, 0.0), Am,
-                             s) ||
-          gemm(false, true, one, Am, Am, Dm))
-        return fail(FGFRFT_ERR_CUDA);
-    }
-    if (fg_zaxpby_identity(N, make_double2(-1.0, 0.0), Cm, one, zero, Dm, s)) return fail(FGFRFT_ERR_CUDA);
-    double2* T = Dm;
-    double2* T2 = Bm;
-    double lnc = 0.0;  // log of the scale c: T^(2^j) = c * (the matrix held in T)
-    const int m0 = W_dev ? 0 : squarings;
-    double glo = 0.0, ghi = 2.0;
-    for (int j = 0;; ++j) {
-      if (fg_ztrace_fro(N, T, nullptr, red, s) || !readback()) return fail(FGFRFT_ERR_CUDA);
-      const double A = h[0], Bq = h[1];
-      const double x = ldexp(1.0, m0 + j);
-      if (!(A > 1e-300) || !(Bq > 0.0)) {  // the complement's powers vanish: every s_k below the bound
-        const double ln_hi = (lnc + log(1e-300)) / x;
-        glo = ln_hi < 0.0 ? 2.0 * sqrt(-expm1(ln_hi)) : 0.0;
-        ghi = 2.0;
-        break;
-      }
-      const double ln_hi = (lnc + log(A)) / x;             // log of the upper bound of s_max
-      const double ln_lo = (lnc + log(Bq) - log(A)) / x;   // log of the lower bound
-      glo = ln_hi < 0.0 ? 2.0 * sqrt(-expm1(ln_hi)) : 0.0;
-      ghi = ln_lo < 0.0 ? 2.0 * sqrt(-expm1(ln_lo)) : 0.0;
-      if ((glo > 0.0 && ghi <= kGapBracket * glo) || m0 + j >= kMaxGapPower) break;
-      // T <- T^2 / ||T||_F^2 (trace 1 for a Hermitian T), c <- c^2 ||T||_F^2
-      if (gemm(false, false, make_double2(1.0 / Bq, 0.0), T, T, T2) || fg_zherm_sym(N, T2, s))
-        return fail(FGFRFT_ERR_CUDA);
-      std::swap(T, T2);
-      lnc = 2.0 * lnc + log(Bq);
-    }
-    p->min_gap_lo = glo;
-    p->min_gap_hi = std::max(glo, ghi);
-  }
+  p->min_gap_lo = gap_lo;
+  p->min_gap_hi = gap_hi;
   p->neg1_tol = neg1_tol;
-  // Classification checks.  Every eigenvalue counted as -1 must be -1 to FP64 accuracy
-  // (the residual, above the rounding of P, which grows as u N / gap), and none left in the
-  // complement may lie within kAmbiguousGap of -1: a spectrum with an eigenvalue between
-  // those two scales has no classification that FP64 can certify.  With a fixed threshold
-  // the separation test above already guards the band around neg1_tol.
-  if (p->r_neg1 > 0) {
-    double thr = 1e-6;
-    if (neg1_tol > 0.0 && !W_dev) {
-      thr = neg1_tol;  // the counted eigenvalues lie below ~0.3 neg1_tol (separation test)
-    } else if (!W_dev) {
-      const double u = 1.1102230246251565e-16;
-      thr = std::max(kResidualFloor, 256.0 * u * (double)N / std::max(p->min_gap_lo, 1e-300));
-      thr = std::min(thr, 1e-6);
-    }
-    if (!(p->proj_residual <= thr * sqrt((double)p->r_neg1))) return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
-  }
-  if (neg1_tol == 0.0 && !W_dev && p->r_neg1 < N && p->min_gap_lo < kAmbiguousGap)
-    return fail(FGFRFT_ERR_AMBIGUOUS_SPECTRUM);
   if (P_dev && cudaMemcpyAsync(P_dev, Cm, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return fail(FGFRFT_ERR_CUDA);
 
@@ -752,7 +808,7 @@ int fgfrft_assemble(fgfrft_plan p, const double* alpha_host, int64_t A, int L, v
     return FGFRFT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   AssembleWork w = carve_assemble(p, (char*)work, A, L);
-  if (!w.tensor && !p->c64 && !p->h32) return FGFRFT_ERR_UNSUPPORTED;
+  if (!w.tensor && !p->c64 && !p->h32 && !(p->real && p->f16)) return FGFRFT_ERR_UNSUPPORTED;
   Staged st(s);
   const double* ad = st.put(a.data(), (size_t)A, w.alpha_dev);
   if (st.failed) return FGFRFT_ERR_CUDA;

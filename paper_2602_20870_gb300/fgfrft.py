@@ -179,7 +179,7 @@ class Plan:
     ``F`` is an N x N unitary matrix (numpy or torch, converted to complex128 on
     the device).  The plan's device memory is a torch uint8 tensor owned here.
     ``neg1_tol``: 0 classifies the lambda = -1 eigenvalues adaptively, a value in
-    [1e-6, 0.5] counts |lambda + 1| below it as -1 (see fgfrft_precompute).
+    [1e-5, 0.5] counts |lambda + 1| below it as -1 (see fgfrft_precompute).
     ``keep_projector``: keep the FP64 projector (complex128 N x N, before rounding) in
     ``self.P64``.  ``self.min_gap`` = (lower, upper) bound of min |lambda + 1| over
     the complement.

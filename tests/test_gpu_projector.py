@@ -46,6 +46,9 @@ def gap_of(d):
     return 2.0 * math.sin(d / 2.0)
 
 
+BR = 1e-7  # slack of the gap bracket checks (FP64 resolution of 1 - g^2/4 for g >= 1e-4)
+
+
 CASES = {
     "tiny graph (det -1)": lambda: W.tiny().F,
     "cyclic shift 64": lambda: W.cyclic_shift(64),
@@ -71,7 +74,8 @@ def test_fp64_projector_gap_and_residual(FG, name):
         assert plan.proj_residual < 1e-12 * math.sqrt(sp.r_neg1)
     lo, hi = plan.min_gap
     g = sp.min_gap
-    assert lo <= g * (1 + 1e-9) and g <= hi * (1 + 1e-9), (lo, g, hi)
+    # FP64 holds s = 1 - g^2/4 to u, so the bracket is exact up to ~u / g^2 relative
+    assert lo <= g * (1 + BR) and g <= hi * (1 + BR), (lo, g, hi)
     assert hi <= 1.0101 * lo
 
 
@@ -92,7 +96,7 @@ def test_caller_supplied_W(FG):
         a, b = own.block(l).cpu().numpy(), given.block(l).cpu().numpy()
         assert np.abs(a - b).max() < 2e-7
     lo, hi = given.min_gap
-    assert lo <= sp.min_gap * (1 + 1e-9) <= hi * (1 + 1e-9) * (1 + 1e-9)
+    assert lo <= sp.min_gap * (1 + BR) and sp.min_gap <= hi * (1 + BR)
     rng = np.random.default_rng(3)
     X = W.complex_normal((70, 64), rng)
     a = rng.uniform(-2, 2, size=70)
@@ -106,7 +110,8 @@ def test_adaptive_classification_refuses_the_uncertifiable_band(FG):
     FP64 cannot certify it as -1 (the residual ||F P + P|| sees 1e-7 above the rounding
     level), and one 4e-7 from -1 stays in the complement closer than 1e-6: both refused.
     1e-11 is -1 to FP64 accuracy and 3e-4 is clearly not: both accepted, as the oracle
-    (tolerance 1e-8) classifies them."""
+    (tolerance 1e-8) classifies them.  (With every other eigenvalue ~0.39 from -1, the widest
+    gap first puts 3e-4 with the exact -1; its residual sends it back to the complement.)"""
     for d in (1e-7, 4e-7):
         F = W.unitary_with_phases(phases(64, 4, near=(d,), exact_neg1=1), 14)
         with pytest.raises(FG.FGFRFTError) as e:
@@ -114,8 +119,13 @@ def test_adaptive_classification_refuses_the_uncertifiable_band(FG):
         assert e.value.code == FG.ERR_AMBIGUOUS_SPECTRUM, d
     for d, r in ((1e-11, 2), (3e-4, 1)):
         F = W.unitary_with_phases(phases(64, 4, near=(d,), exact_neg1=1), 14)
-        plan = FG.Plan(F, 4)
-        assert plan.r_neg1 == r == O.spectral(F).r_neg1, d
+        plan = FG.Plan(F, 4, keep_projector=True)
+        sp = O.spectral(F)
+        assert plan.r_neg1 == r == sp.r_neg1, d
+        assert rel(plan.P64.cpu().numpy(), O.projector(F, sp)) < 1e-8
+        if d == 3e-4:
+            lo, hi = plan.min_gap
+            assert lo <= gap_of(d) * (1 + BR) and gap_of(d) <= hi * (1 + BR)
 
 
 def test_fixed_threshold_classification(FG):
@@ -132,7 +142,7 @@ def test_fixed_threshold_classification(FG):
     assert rel(plan.P64.cpu().numpy(), O.projector(F, sp)) < 1e-8
     assert abs(plan.proj_residual - gap_of(d_in)) < 1e-3 * gap_of(d_in)
     lo, hi = plan.min_gap
-    assert lo <= gap_of(d_out) * (1 + 1e-9) and gap_of(d_out) <= hi * (1 + 1e-9) and hi <= 1.0101 * lo
+    assert lo <= gap_of(d_out) * (1 + BR) and gap_of(d_out) <= hi * (1 + BR) and hi <= 1.0101 * lo
     # transforms from this plan follow Def. 1 with the oracle's P at the same tolerance
     rng = np.random.default_rng(6)
     X = W.complex_normal((20, 64), rng)
