@@ -761,6 +761,7 @@ int fgfrft_plan_status(fgfrft_plan p, void* stream) {
     CK(cudaStreamSynchronize(s));
   }
   if (w & FG_STATUS_WAIT_TIMEOUT) return FGFRFT_ERR_TIMEOUT;
+  if (w & FG_STATUS_LAUNCH_MISMATCH) return FGFRFT_ERR_CUDA;
   return FGFRFT_OK;
 }
 

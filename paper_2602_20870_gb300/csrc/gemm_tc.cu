@@ -35,8 +35,9 @@
 namespace {
 
 constexpr int TC_BM = 128;                 // rows per tile (TMEM lanes)
-constexpr int TC_KC = 32;                  // k per stage: 32 fp16 = 64-byte rows
-constexpr int TC_PLANE_A = TC_BM * TC_KC * 2;  // 8 KB
+// k per chunk: 32 fp16 = 64-byte rows (64-byte swizzle), or KC = 64 = 128-byte rows
+// (128-byte swizzle), which the tensor-map loads serve from L2 at a higher rate
+constexpr int TC_KC = 32;
 constexpr int TC_EPI_WARP0 = 2;  // warps before the epilogue: the producer and the MMA issuer
 constexpr int TC_MAXBUF = 8;     // TMEM accumulator buffers at most
 constexpr int TC_BN_MAX = 256;
@@ -48,9 +49,10 @@ constexpr int TC_BN_STD = 128;  // column-tile width of the stacked and complex 
 constexpr int TC_RB_MAXCH = 5;  // resident-B mode: at most 5 k-chunks (K <= 160)
 // RA ("real A"): the A operand is real (its imaginary planes are zero), so only the two
 // real planes are loaded and each k16 step issues 6 MMAs (Ar*Xr, Ar*Xi) instead of 12.
-template <int BN, bool RB = false, bool RA = false>
+template <int BN, bool RB = false, bool RA = false, int KC = TC_KC>
 struct TcCfg {
-  static constexpr int PLANE_B = BN * TC_KC * 2;
+  static constexpr int PLANE_A = TC_BM * KC * 2;
+  static constexpr int PLANE_B = BN * KC * 2;
   static constexpr int A_PLANES = RA ? 2 : 4;
   // Epilogue warps: 8, or 16 for the resident-B launch (the fused assembly), whose few MMAs
   // per tile leave the epilogue (TMEM -> fp16 hi/lo -> global) as the critical path: four
@@ -119,6 +121,11 @@ struct TcParams {
   // of the tail map (its missing columns read as zeros)
   int a_chunked;
   int a_nfull;
+  // narrow tail (chunk-major A with the resident B and every chunk of a tile in one stage):
+  // the tail chunk is a 16-column box with 32-byte swizzle (4 KB per plane, one k16 step)
+  // instead of a 32-column one, so a stage holds no zero-filled columns
+  int a_tail16;
+  int stage_bytes;    // nonzero: the stage size the host computed for this layout
   const int* bimag;   // NULL, or a device word that is 0 when every B column is real
   const float2* coef;
   const float2* coefd;
@@ -137,6 +144,33 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
   d |= (uint64_t)1 << 46;                     // descriptor version
   d |= (uint64_t)4 << 61;                     // 64-byte swizzle
   return d;
+}
+
+// K-major operand with 32-byte rows and 32-byte swizzle (8-row atoms of 256 bytes)
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(256 >> 4) << 32;            // stride byte offset: 8 rows x 32 B
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)6 << 61;                     // 32-byte swizzle
+  return d;
+}
+
+// K-major operand with 128-byte rows and 128-byte swizzle (8-row atoms of 1 KB)
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+
+template <int KC>
+__device__ __forceinline__ uint64_t desc_kc(uint32_t saddr) {
+  return KC == 64 ? desc_sw128(saddr) : desc_sw64(saddr);
 }
 
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
@@ -246,11 +280,13 @@ __device__ __forceinline__ void epi_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
 }
 
-template <int BN, bool RB, bool RA>
-__global__ void __launch_bounds__(TcCfg<BN, RB, RA>::THREADS, 1)
+template <int BN, bool RB, bool RA, int KC>
+__global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmT, TcParams p) {
-  using Cfg = TcCfg<BN, RB, RA>;
+  using Cfg = TcCfg<BN, RB, RA, KC>;
+  static_assert(KC == 32 || (KC == 64 && !RB), "128-byte k-chunks: streamed B only");
+  constexpr int PLANE_A = Cfg::PLANE_A;
   constexpr int A_PLANES = Cfg::A_PLANES;
   constexpr int TC_BN = BN;
   constexpr int TC_PLANE_B = Cfg::PLANE_B;
@@ -271,13 +307,22 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA>::THREADS, 1)
   const bool breal = p.bimag != nullptr && *p.bimag == 0;
   const bool re_only = RA && (p.re_only || breal);
   const int nbp = (re_only || breal) ? 2 : 4;  // B planes loaded
-  uint8_t* const bres = sbase + sizeof(TcCtl);  // resident B: [chunk][4 planes][BN rows x 64 B]
-  const int res_bytes = RB ? p.kchunks * 4 * TC_PLANE_B : 0;
+  uint8_t* const bres = sbase + sizeof(TcCtl);  // resident B: [chunk][nbp planes][BN rows x 64 B]
+  const int res_bytes = RB ? p.kchunks * nbp * TC_PLANE_B : 0;
   uint8_t* const stages = bres + res_bytes;
-  const int chunk_bytes = A_PLANES * TC_PLANE_A + (RB ? 0 : nbp * TC_PLANE_B);
+  const int chunk_bytes = A_PLANES * PLANE_A + (RB ? 0 : nbp * TC_PLANE_B);
   const int cps = p.cps > 1 ? p.cps : 1;
-  const int stage_bytes = cps * chunk_bytes;
+  // narrow tail: chunk c < a_nfull at c * chunk_bytes, the tail after them, TAIL_PLANE apart
+  constexpr int TAIL_PLANE = TC_BM * 32;
+  const bool tail16 = RB && p.a_chunked && p.a_tail16 && cps >= p.kchunks;
+  const int stage_bytes = p.stage_bytes ? p.stage_bytes : cps * chunk_bytes;
   const int nst = min(TC_MAXST, (p.smem_bytes - (int)sizeof(TcCtl) - res_bytes) / stage_bytes);
+  // a launch sized for real signals whose split reports an imaginary part (or any other
+  // mismatch of the host's sizing): record it and return before anything is set up
+  if (nst < 1 || (p.stage_bytes && !tail16 && cps * chunk_bytes > p.stage_bytes)) {
+    if (threadIdx.x == 0) atomicOr(p.status, FG_STATUS_LAUNCH_MISMATCH);
+    return;
+  }
   // TMEM columns of one accumulator buffer, and how many buffers fit (2: the epilogue of one
   // block overlaps the MMAs of the next)
   const bool merged = Cfg::MERGE && re_only;
@@ -331,7 +376,7 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA>::THREADS, 1)
         mbar_arrive_expect_tx(&sm.bfull, (uint32_t)(p.kchunks * nbp * TC_PLANE_B));
         for (int kc = 0; kc < p.kchunks; ++kc)
           for (int q = 0; q < nbp; ++q)
-            tma_load_3d(bres + (kc * 4 + q) * TC_PLANE_B, &tmB, kc * TC_KC, next.z, q, &sm.bfull);
+            tma_load_3d(bres + (kc * nbp + q) * TC_PLANE_B, &tmB, kc * KC, next.z, q, &sm.bfull);
         b_issued = true;
       }
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
@@ -351,28 +396,28 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA>::THREADS, 1)
               break;
             }
             const int nc = min(cps, p.kchunks - kc0);
-            mbar_arrive_expect_tx(&sm.full[s], (uint32_t)(nc * chunk_bytes));
+            mbar_arrive_expect_tx(&sm.full[s], (uint32_t)(tail16 ? stage_bytes : nc * chunk_bytes));
             issued[s]++;
             for (int c = 0; c < nc; ++c) {
               uint8_t* st = stages + s * stage_bytes + c * chunk_bytes;
-              const int k0 = (kc0 + c) * TC_KC;
+              const int k0 = (kc0 + c) * KC;
               if (p.a_chunked) {  // chunk-major A: full 32-column chunk planes, then the tail
                 const int kc = kc0 + c;
 #pragma unroll
                 for (int q = 0; q < A_PLANES; ++q) {
                   if (kc < p.a_nfull)
-                    tma_load_3d(st + q * TC_PLANE_A, &tmA, 0, tile.x * TC_BM, q * p.a_nfull + kc, &sm.full[s]);
+                    tma_load_3d(st + q * PLANE_A, &tmA, 0, tile.x * TC_BM, q * p.a_nfull + kc, &sm.full[s]);
                   else
-                    tma_load_3d(st + q * TC_PLANE_A, &tmT, 0, tile.x * TC_BM, q, &sm.full[s]);
+                    tma_load_3d(st + q * (tail16 ? TAIL_PLANE : PLANE_A), &tmT, 0, tile.x * TC_BM, q, &sm.full[s]);
                 }
               } else {
 #pragma unroll
                 for (int q = 0; q < A_PLANES; ++q)
-                  tma_load_3d(st + q * TC_PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
+                  tma_load_3d(st + q * PLANE_A, &tmA, k0, tile.x * TC_BM, zA + q, &sm.full[s]);
               }
               if (!RB) {
                 for (int q = 0; q < nbp; ++q)
-                  tma_load_3d(st + A_PLANES * TC_PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
+                  tma_load_3d(st + A_PLANES * PLANE_A + q * TC_PLANE_B, &tmB, k0, tile.z, q, &sm.full[s]);
               }
             }
           }
@@ -438,14 +483,19 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA>::THREADS, 1)
             for (int c = 0; c < nc; ++c) {
             const int kc = kc0 + c;
             const uint32_t sa = smem_u32(stages + s * stage_bytes + c * chunk_bytes);
-            const uint32_t sb = RB ? smem_u32(bres + kc * 4 * TC_PLANE_B) : sa + A_PLANES * TC_PLANE_A;
+            const uint32_t sb = RB ? smem_u32(bres + kc * nbp * TC_PLANE_B) : sa + A_PLANES * PLANE_A;
+            // the narrow tail: 32-byte rows (one k16 step), 32-byte swizzle
+            const bool is_tail = tail16 && kc >= p.a_nfull;
+            const uint32_t apl = is_tail ? (uint32_t)TAIL_PLANE : (uint32_t)PLANE_A;
+            auto adesc = [&](uint32_t a) { return is_tail ? desc_sw32(a) : desc_kc<KC>(a); };
 #pragma unroll
-            for (int kk = 0; kk < TC_KC / 16; ++kk) {
+            for (int kk = 0; kk < KC / 16; ++kk) {
+              if (is_tail && kk > 0) continue;
               const uint32_t off = kk * 32;  // 16 fp16 along k
-              const uint64_t arh = desc_sw64(sa + 0 * TC_PLANE_A + off), arl = desc_sw64(sa + 1 * TC_PLANE_A + off);
-              const uint64_t brh = desc_sw64(sb + 0 * TC_PLANE_B + off), brl = desc_sw64(sb + 1 * TC_PLANE_B + off);
-              const uint64_t bih = desc_sw64(sb + 2 * TC_PLANE_B + off), bil = desc_sw64(sb + 3 * TC_PLANE_B + off);
-              if (p.kvalid > 0 && kc * TC_KC + kk * 16 >= p.kvalid) continue;  // all-zero k16 step
+              const uint64_t arh = adesc(sa + 0 * apl + off), arl = adesc(sa + 1 * apl + off);
+              const uint64_t brh = desc_kc<KC>(sb + 0 * TC_PLANE_B + off), brl = desc_kc<KC>(sb + 1 * TC_PLANE_B + off);
+              const uint64_t bih = desc_kc<KC>(sb + 2 * TC_PLANE_B + off), bil = desc_kc<KC>(sb + 3 * TC_PLANE_B + off);
+              if (p.kvalid > 0 && kc * KC + kk * 16 >= p.kvalid) continue;  // all-zero k16 step
               const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
               if (merged) {  // [A_hi*B_hi | A_hi*B_lo], then A_lo*B_hi into the first half
                 umma(d_re, arh, brh, Cfg::IDESC_2N, acc);
@@ -459,7 +509,7 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA>::THREADS, 1)
               if (re_only) continue;  // real product: no imaginary accumulator
               if (breal) {            // complex A, real X: Im = Ai*Xr only
                 if (!RA) {
-                  const uint64_t aih = desc_sw64(sa + 2 * TC_PLANE_A + off), ail = desc_sw64(sa + 3 * TC_PLANE_A + off);
+                  const uint64_t aih = adesc(sa + 2 * apl + off), ail = adesc(sa + 3 * apl + off);
                   umma(d_im, aih, brh, idesc, acc);
                   umma(d_im, aih, brl, idesc, 1);
                   umma(d_im, ail, brh, idesc, 1);
@@ -471,7 +521,7 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA>::THREADS, 1)
               umma(d_im, arh, bil, idesc, 1);
               umma(d_im, arl, bih, idesc, 1);
               if (!RA) {
-                const uint64_t aih = desc_sw64(sa + 2 * TC_PLANE_A + off), ail = desc_sw64(sa + 3 * TC_PLANE_A + off);
+                const uint64_t aih = adesc(sa + 2 * apl + off), ail = adesc(sa + 3 * apl + off);
                 umma(d_re, aih, bih, idesc_neg, 1);
                 umma(d_re, aih, bil, idesc_neg, 1);
                 umma(d_re, ail, bih, idesc_neg, 1);
@@ -659,10 +709,10 @@ EncodeTiledFn encode_fn() {
 }
 
 // 3-D fp16 map: dim0 = k (N, contiguous), dim1 = rows (pitch Np), dim2 = planes (stride plane_elems);
-// 32 k x box_rows boxes, 64-byte swizzle (the MMA operand layout).
+// kc k x box_rows boxes, 2 kc-byte swizzle (the MMA operand layout of a kc-wide k-chunk).
 bool make_map(CUtensorMap* m, const void* base, int64_t N, int64_t rows, int64_t Np, int64_t nplanes,
-              int64_t plane_elems, int box_rows) {
-  return fg_make_map_f16(m, base, N, rows, Np, nplanes, plane_elems, TC_KC, box_rows, 64);
+              int64_t plane_elems, int box_rows, int kc = TC_KC) {
+  return fg_make_map_f16(m, base, N, rows, Np, nplanes, plane_elems, kc, box_rows, 2 * kc);
 }
 
 }  // namespace
@@ -708,14 +758,18 @@ int sm_count() {
   return n;
 }
 
-template <int BN, bool RB, bool RA>
+template <int BN, bool RB, bool RA, int KC = TC_KC>
 cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mT, int ntiles,
                       const TcParams& p, cudaStream_t s, int kclass) {
   // all the shared memory a CTA may have (one CTA per SM); the kernel sizes its ring to it
   const int smem = smem_optin();
-  using Cfg = TcCfg<BN, RB, RA>;
-  const int res_bytes = RB ? p.kchunks * 4 * Cfg::PLANE_B : 0;
-  const int worst_stage = (p.cps > 1 ? p.cps : 1) * (Cfg::A_PLANES * TC_PLANE_A + (RB ? 0 : 4 * Cfg::PLANE_B));
+  using Cfg = TcCfg<BN, RB, RA, KC>;
+  // resident B: the planes the kernel loads (2 when the product is real by construction; a
+  // real B found on the device only leaves more room for the ring)
+  const int res_bytes = RB ? p.kchunks * ((RA && p.re_only) ? 2 : 4) * Cfg::PLANE_B : 0;
+  const int worst_stage =
+      p.stage_bytes ? p.stage_bytes
+                    : (p.cps > 1 ? p.cps : 1) * (Cfg::A_PLANES * Cfg::PLANE_A + (RB ? 0 : 4 * Cfg::PLANE_B));
   TcParams q = p;
   q.smem_bytes = smem - 1024;  // the kernel aligns its base up to 1024 bytes
   if (q.smem_bytes - (int)sizeof(TcCtl) - res_bytes < TC_MIN_STAGES * worst_stage) return cudaErrorInvalidValue;
@@ -728,11 +782,11 @@ cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, const CUtens
     smem_req = q.smem_bytes + 1024;
   }
   cudaError_t e =
-      cudaFuncSetAttribute(tc_gemm_kernel<BN, RB, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_req);
+      cudaFuncSetAttribute(tc_gemm_kernel<BN, RB, RA, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_req);
   if (e != cudaSuccess) return e;
   const int grid = std::min<int>(ntiles, sm_count());
   FgTimed timed(kclass, s);
-  tc_gemm_kernel<BN, RB, RA><<<grid, Cfg::THREADS, smem_req, s>>>(mA, mB, mT, q);
+  tc_gemm_kernel<BN, RB, RA, KC><<<grid, Cfg::THREADS, smem_req, s>>>(mA, mB, mT, q);
   fg_note_launch(kclass);
   return cudaGetLastError();
 }
@@ -741,7 +795,8 @@ cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, const CUtens
 // resident_b: every tile has the same columns (needs bn == 64 and kchunks <= TC_RB_MAXCH).
 cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vector<int4>& tiles, TcParams p,
                    void* scratch, size_t scratch_bytes, cudaStream_t s, int kclass = FGFRFT_KC_TC_GEMM,
-                   int bn = 128, bool resident_b = false, bool real_a = false, const CUtensorMap* mTail = nullptr) {
+                   int bn = 128, bool resident_b = false, bool real_a = false, const CUtensorMap* mTail = nullptr,
+                   int kc = TC_KC) {
   const CUtensorMap& mT = mTail ? *mTail : mA;  // the tail map is read only with p.a_chunked
   if (p.a_chunked && !mTail) return cudaErrorInvalidValue;
   if (tiles.empty()) {
@@ -760,6 +815,17 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vect
     return real_a ? launch_bn<64, true, true>(mA, mB, mT, p.ntiles, p, s, kclass)
                   : launch_bn<64, true, false>(mA, mB, mT, p.ntiles, p, s, kclass);
   }
+  if (kc == 64) {  // 128-byte k-chunks (the caller checked that two stages fit)
+    if (bn == 256) {
+      if (!real_a) return cudaErrorInvalidValue;
+      return launch_bn<256, false, true, 64>(mA, mB, mT, p.ntiles, p, s, kclass);
+    }
+    if (bn == 64)
+      return real_a ? launch_bn<64, false, true, 64>(mA, mB, mT, p.ntiles, p, s, kclass)
+                    : launch_bn<64, false, false, 64>(mA, mB, mT, p.ntiles, p, s, kclass);
+    return real_a ? launch_bn<128, false, true, 64>(mA, mB, mT, p.ntiles, p, s, kclass)
+                  : launch_bn<128, false, false, 64>(mA, mB, mT, p.ntiles, p, s, kclass);
+  }
   if (bn == 256) {  // real A only (a complex A at BN = 256 leaves too few stages)
     if (!real_a) return cudaErrorInvalidValue;
     return launch_bn<256, false, true>(mA, mB, mT, p.ntiles, p, s, kclass);
@@ -769,6 +835,21 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vect
                   : launch_bn<64, false, false>(mA, mB, mT, p.ntiles, p, s, kclass);
   return real_a ? launch_bn<128, false, true>(mA, mB, mT, p.ntiles, p, s, kclass)
                 : launch_bn<128, false, false>(mA, mB, mT, p.ntiles, p, s, kclass);
+}
+
+// k-chunk width of a streamed-B launch: 64 (128-byte rows, which the tensor-map loads serve
+// from L2 faster than 64-byte rows) when two ring stages of it fit in shared memory, else 32.
+// b_real: every B column is known to be real (real float32 signals), so a stage needs only
+// the two real B planes; *stage_bytes then receives that stage size (0 otherwise).  Used by
+// the stacked GEMM, whose tiles stream every stored block against one signal tile (measured
+// 18% faster than 32-wide chunks at N = 1024); the grouped GEMM keeps 32-wide chunks (its
+// 256-column tiles fit four 48 KB stages instead of two 96 KB ones, measured 8% faster).
+int pick_kc(int bn, bool real_a, bool b_real, int* stage_bytes) {
+  const int st = (real_a ? 2 : 4) * TC_BM * 64 * 2 + (b_real ? 2 : 4) * bn * 64 * 2;
+  *stage_bytes = 0;
+  if (TC_MIN_STAGES * st + (int)sizeof(TcCtl) + 1024 > smem_optin()) return TC_KC;
+  if (b_real) *stage_bytes = st;
+  return 64;
 }
 
 }  // namespace
@@ -833,9 +914,10 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   }
   // real operators: 256-column tiles halve the re-reads of each operator tile from L2
   const int bn = fg_tc_grouped_bn(a.real_a);
+  const int kc = TC_KC, stage_bytes = 0;
   CUtensorMap mA, mB;
-  if (!make_map(&mA, a.Qs, a.N, a.N, a.Np, 4 * a.groups, a.plane_elems, TC_BM) ||
-      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, bn))
+  if (!make_map(&mA, a.Qs, a.N, a.N, a.Np, 4 * a.groups, a.plane_elems, TC_BM, kc) ||
+      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, bn, kc))
     return cudaErrorInvalidValue;
   std::vector<int4> tiles;
   TcParams p{};
@@ -848,13 +930,15 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   p.nblk = 1;
   p.grouped = 1;
   p.rows = a.N;
-  p.kchunks = (int)((a.N + TC_KC - 1) / TC_KC);
+  p.kchunks = (int)((a.N + kc - 1) / kc);
+  p.stage_bytes = stage_bytes;
   p.Y = a.Y;
   p.col_exp = a.col_exp;
   p.status = a.status;
   p.bimag = a.bimag;
   p.y_real = a.y_real ? 1 : 0;
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, bn, false, a.real_a);
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, bn, false, a.real_a, nullptr,
+                kc);
 }
 
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
@@ -863,8 +947,10 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
   const int64_t nplanes = 4 * (int64_t)(std::max(a.b0 + a.nb_pow, a.p_blk + 1));
-  if (!make_map(&mA, a.stack, a.N, a.N, a.Np, nplanes, a.plane_elems, TC_BM) ||
-      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN_STD))
+  int stage_bytes = 0;
+  const int kc = pick_kc(TC_BN_STD, a.real_a, a.x_real, &stage_bytes);
+  if (!make_map(&mA, a.stack, a.N, a.N, a.Np, nplanes, a.plane_elems, TC_BM, kc) ||
+      !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, TC_BN_STD, kc))
     return cudaErrorInvalidValue;
   std::vector<int4> tiles;
   const int row_tiles = (int)((a.N + TC_BM - 1) / TC_BM);
@@ -878,7 +964,8 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   p.nb_pow = a.nb_pow;
   p.p_blk = a.p_blk;
   p.rows = a.N;
-  p.kchunks = (int)((a.N + TC_KC - 1) / TC_KC);
+  p.kchunks = (int)((a.N + kc - 1) / kc);
+  p.stage_bytes = stage_bytes;
   p.coef = a.coef;
   p.coefd = a.coefd;
   p.ldcoef = a.B;
@@ -887,7 +974,8 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   p.col_exp = a.col_exp;
   p.status = a.status;
   p.bimag = a.bimag;
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, 128, false, a.real_a);
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, 128, false, a.real_a, nullptr,
+                kc);
 }
 
 cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
@@ -903,10 +991,15 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   if (a.Kp % 8 || a.Kp < a.K) return cudaErrorInvalidValue;
   CUtensorMap mA, mB, mT;
   const __half* tail = a.entry_stack + 4 * nfull * a.planeT * TC_KC;
+  // one column tile (A <= 64): the coefficient operand stays resident in shared memory
+  const bool rb = bn == 64 && (a.K + TC_KC - 1) / TC_KC <= TC_RB_MAXCH;
+  // a tail of at most 16 columns is read as a 16-column box with 32-byte swizzle (the box
+  // carries no more than 8 zero-filled columns, 4 KB per plane instead of 8 KB)
+  const bool tail16 = rb && wtail > 0 && wtail <= 16;
   if ((nfull > 0 && !fg_make_map_f16(&mA, a.entry_stack, TC_KC, a.entries, TC_KC, 4 * nfull, a.planeT * TC_KC,
                                       TC_KC, TC_BM, 64)) ||
-      (wtail > 0 &&
-       !fg_make_map_f16(&mT, tail, wtail, a.entries, wtail, 4, a.planeT * wtail, TC_KC, TC_BM, 64)) ||
+      (wtail > 0 && !fg_make_map_f16(&mT, tail, wtail, a.entries, wtail, 4, a.planeT * wtail, tail16 ? 16 : TC_KC,
+                                     TC_BM, tail16 ? 32 : 64)) ||
       !make_map(&mB, a.Cs, a.K, a.A, a.Kp, 4, a.A * a.Kp, bn))
     return cudaErrorInvalidValue;
   if (nfull == 0) mA = mT;
@@ -941,11 +1034,14 @@ cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
   p.re_only = a.re_only && a.real_a ? 1 : 0;
   // one exponent for every coefficient column (FG_COEF_EXP)
   p.uscale = ldexpf(1.0f, a.Qs ? -FG_COEF_EXP : -(FG_SPLIT_SHIFT + FG_COEF_EXP));
-  // one column tile (A <= 64): the coefficient operand stays resident in shared memory
-  const bool rb = bn == 64 && p.kchunks <= TC_RB_MAXCH;
   // the k-chunks of a tile are few (K = 2L+2 stored blocks): group them into one ring stage,
-  // as many as leave room for two stages
-  {
+  // as many as leave room for two stages (all of them with the narrow tail)
+  if (tail16) {
+    const int ap = a.real_a ? 2 : 4;
+    p.a_tail16 = 1;
+    p.cps = p.kchunks;
+    p.stage_bytes = (int)nfull * ap * TC_BM * TC_KC * 2 + ap * TC_BM * 32;
+  } else {
     const int plane_b = bn * TC_KC * 2;
     const int chunk = (a.real_a ? 2 : 4) * TC_BM * TC_KC * 2 + (rb ? 0 : 4 * plane_b);
     const int res = rb ? p.kchunks * 4 * plane_b : 0;

@@ -54,6 +54,7 @@ static inline int blk_of_P(const fgfrft_plan_s* p) { return 2 * p->L_max + 1; }
 
 // Device status codes (OR-ed into the plan's status word).
 #define FG_STATUS_WAIT_TIMEOUT 1u
+#define FG_STATUS_LAUNCH_MISMATCH 2u  // a kernel found its launch sizing unusable and did nothing
 
 // Bounded waits give up after this many nanoseconds of %globaltimer.
 #define FG_WAIT_LIMIT_NS 2000000000ull
