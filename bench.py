@@ -777,7 +777,8 @@ def run_point_cloud(args):
             Y, D = plan.forward_dual(wl.alpha, X, L, path=path)
             plan.backward(wl.alpha, G, D, L, path=path)
         ms = _device_time(step, args.steps, args.warmup)
-        flops = 3 * 8.0 * (2 * L + 2) * N * N * B  # forward (dual) + adjoint, algorithmic
+        # forward (dual) + adjoint, algorithmic (real F: a real block times a complex signal)
+        flops = 3 * (4.0 if plan.real else 8.0) * (2 * L + 2) * N * N * B
         out[path] = {"ms_per_step": ms, "signals_per_s": B / (ms / 1e3), "algorithmic_tflops": flops / ms / 1e9}
     line = {"metric": "signals/s (forward + dY/dalpha + adjoint + alpha-gradient)", "workload": wl.name,
             "value": out["stacked"]["signals_per_s"], "unit": "signals/s", "paths": out, "clocks": clk.stop()}

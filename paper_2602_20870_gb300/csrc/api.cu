@@ -340,6 +340,8 @@ struct ApplyWork {
   int* bimag = nullptr;
   double* partials = nullptr;
   int2* gtab = nullptr;
+  float2* ysplit = nullptr;  // stacked path: partial sums of the block splits
+  float2* dsplit = nullptr;
   void* tc_scratch = nullptr;
   size_t tc_scratch_bytes = 0;
   int64_t xs_rows = 0;
@@ -384,9 +386,15 @@ ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int 
       if (base) w.asm_work = carve_assemble(p, w.asm_base, groups, L, dual);
       break;
     }
-    case FGFRFT_PATH_STACKED:
+    case FGFRFT_PATH_STACKED: {
       w.coef = c.take<float2>((size_t)nb * B);
       w.coefd = c.take<float2>((size_t)nb * B);
+      // partial sums of the block splits (few tiles: each tile's blocks over several CTAs)
+      const int splits = fg_tc_stacked_splits(p->N, B, nb);
+      if (splits > 1) {
+        w.ysplit = c.take<float2>((size_t)splits * B * p->N);
+        if (dual) w.dsplit = c.take<float2>((size_t)splits * B * p->N);
+      }
       w.xs_rows = fg_tc_signal_rows(B, 1);
       w.Xs = c.take<__half>((size_t)4 * w.xs_rows * p->Np);
       w.col_exp = c.take<int>((size_t)w.xs_rows);
@@ -394,6 +402,7 @@ ApplyWork carve_apply(const fgfrft_plan_s* p, char* base, int64_t B, int L, int 
       w.tc_scratch_bytes = fg_tc_scratch_bytes(p->N, B, 1, nb);
       w.tc_scratch = c.take<char>(w.tc_scratch_bytes);
       break;
+    }
     default:
       break;
   }
@@ -996,6 +1005,8 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, const Runs& runs, i
       ta.real_a = p->real;
       ta.bimag = w.bimag;
       ta.x_real = x_real;
+      ta.Ysplit = w.ysplit;
+      ta.Dsplit = w.dsplit;
       CK(fg_tc_stacked_apply(ta, s));
       return FGFRFT_OK;
     }

@@ -126,6 +126,10 @@ struct TcParams {
   // instead of a 32-column one, so a stage holds no zero-filled columns
   int a_tail16;
   int stage_bytes;    // nonzero: the stage size the host computed for this layout
+  // stacked tiles split over the stored blocks: tile.y = s takes blocks [s * bps, (s + 1) * bps)
+  // and writes its partial sums at Y + s * split_stride (D likewise); bps = 0: no split
+  int bps;
+  int64_t split_stride;
   const int* bimag;   // NULL, or a device word that is 0 when every B column is real
   const float2* coef;
   const float2* coefd;
@@ -232,6 +236,13 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, Smem& sm
 
 __device__ __forceinline__ int4 tile_of(const TcParams& p, int t) {
   return p.tiles ? p.tiles[t] : make_int4(t, 0, 0, p.arith_cols);
+}
+
+// the blocks a tile accumulates: all of them, or its split's range
+__device__ __forceinline__ int2 blk_range(const TcParams& p, const int4& tl) {
+  if (p.grouped || p.bps == 0) return make_int2(0, p.nblk);
+  const int b0 = tl.y * p.bps;
+  return make_int2(b0, min(b0 + p.bps, p.nblk));
 }
 
 // Split-output epilogue of one CW-column chunk: column j0 + c of this thread's row goes to
@@ -382,7 +393,8 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
         const int4 tile = next;
         if (t + (int)gridDim.x < p.ntiles) next = tile_of(p, t + gridDim.x);  // prefetch
-        for (int b = 0; ok && b < p.nblk; ++b) {
+        const int2 br = blk_range(p, tile);
+        for (int b = br.x; ok && b < br.y; ++b) {
           const int zA = p.grouped ? tile.y : 4 * (b < p.nb_pow ? p.b0 + b : p.p_blk);
           for (int kc0 = 0; kc0 < p.kchunks; kc0 += cps) {
             const int s = s_cur;
@@ -458,7 +470,8 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
           idesc = (kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(n16 >> 3) << 17);
           idesc_neg = idesc | (1u << 13);
         }
-        for (int b = 0; ok && b < p.nblk; ++b, ++bc) {
+        const int2 br = blk_range(p, p.bps && !p.grouped ? tile_of(p, t) : make_int4(0, 0, 0, 0));
+        for (int b = br.x; ok && b < br.y; ++b, ++bc) {
           const uint32_t buf = bc % (uint32_t)nbuf, tph = (bc / (uint32_t)nbuf) & 1;
           if (!tc_wait(&sm.tempty[buf], tph ^ 1, sm, p.status)) {
             ok = false;
@@ -587,7 +600,9 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
         qoff = qi * p.qNp + (gi - qi * p.qN);
       }
 
-      for (int b = 0; b < p.nblk; ++b, ++bc) {
+      const int2 br = blk_range(p, tile);
+      const int64_t split_off = (p.bps && !p.grouped) ? (int64_t)tile.y * p.split_stride : 0;
+      for (int b = br.x; b < br.y; ++b, ++bc) {
         if (!mine) continue;  // the other group's tile (its buffer index still counts)
         const uint32_t buf = bc % (uint32_t)nbuf, tph = (bc / (uint32_t)nbuf) & 1;
         if (!tc_wait(&sm.tfull[buf], tph, sm, p.status)) {
@@ -645,29 +660,34 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
               yp += p.rows;
             }
           } else {
-            float2* yp = p.Y + (int64_t)j0 * p.rows + gi;
-            float2* dp = p.D ? p.D + (int64_t)j0 * p.rows + gi : nullptr;
+            // Y (may be absent: the dual alone) and D accumulate block by block; the first
+            // block of the tile's range starts them
+            float2* yp = p.Y ? p.Y + split_off + (int64_t)j0 * p.rows + gi : nullptr;
+            float2* dp = p.D ? p.D + split_off + (int64_t)j0 * p.rows + gi : nullptr;
             const float2* cfp = p.coef + (int64_t)b * p.ldcoef + j0;
             const float2* cdp = p.D ? p.coefd + (int64_t)b * p.ldcoef + j0 : nullptr;
+            const bool first = b == br.x;
 #pragma unroll
             for (int c = 0; c < CW; ++c) {
               if (c < ncol) {
                 const float sc = sm.scale[cc * CW + c];
                 const float tr = __uint_as_float(vr[c]) * sc, ti = __uint_as_float(vi[c]) * sc;
-                const float2 cf = __ldg(cfp + c);
-                float2 y = b == 0 ? make_float2(0.f, 0.f) : *yp;
-                y.x = fmaf(cf.x, tr, fmaf(-cf.y, ti, y.x));
-                y.y = fmaf(cf.x, ti, fmaf(cf.y, tr, y.y));
-                *yp = y;
+                if (yp) {
+                  const float2 cf = __ldg(cfp + c);
+                  float2 y = first ? make_float2(0.f, 0.f) : *yp;
+                  y.x = fmaf(cf.x, tr, fmaf(-cf.y, ti, y.x));
+                  y.y = fmaf(cf.x, ti, fmaf(cf.y, tr, y.y));
+                  *yp = y;
+                }
                 if (dp) {
                   const float2 cd = __ldg(cdp + c);
-                  float2 d = b == 0 ? make_float2(0.f, 0.f) : *dp;
+                  float2 d = first ? make_float2(0.f, 0.f) : *dp;
                   d.x = fmaf(cd.x, tr, fmaf(-cd.y, ti, d.x));
                   d.y = fmaf(cd.x, ti, fmaf(cd.y, tr, d.y));
                   *dp = d;
                 }
               }
-              yp += p.rows;
+              if (yp) yp += p.rows;
               if (dp) dp += p.rows;
             }
           }
@@ -869,10 +889,12 @@ bool fg_tc_available() {
 
 int64_t fg_tc_signal_rows(int64_t B, int64_t) { return B; }
 
-size_t fg_tc_scratch_bytes(int64_t N, int64_t B, int64_t groups, int) {
+size_t fg_tc_scratch_bytes(int64_t N, int64_t B, int64_t groups, int nblk) {
   const int64_t row_tiles = (N + TC_BM - 1) / TC_BM;
   const int64_t col_tiles = (B + 63) / 64 + groups;  // each group may add a ragged tile (tiles >= 64 wide)
-  return (size_t)(row_tiles * col_tiles) * sizeof(int4) + 256;
+  // stacked tiles repeat once per block split
+  const int64_t splits = nblk > 1 ? fg_tc_stacked_splits(N, B, nblk) : 1;
+  return (size_t)(row_tiles * col_tiles * splits) * sizeof(int4) + 256;
 }
 
 int fg_tc_grouped_bn(bool real_a) { return real_a ? 256 : TC_BN_STD; }
@@ -954,11 +976,20 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
   std::vector<int4> tiles;
   const int row_tiles = (int)((a.N + TC_BM - 1) / TC_BM);
-  for (int rt = 0; rt < row_tiles; ++rt)
-    for (int64_t c = 0; c < a.B; c += TC_BN_STD)
-      tiles.push_back(make_int4(rt, 0, (int)c, (int)std::min<int64_t>(c + TC_BN_STD, a.B)));
+  const int nblk = a.nb_pow + (a.p_blk >= 0 ? 1 : 0);
+  // few tiles (small batches): each tile's blocks are split over several CTAs, whose partial
+  // sums are added in a fixed order afterwards (deterministic)
+  const int splits = fg_tc_stacked_splits(a.N, a.B, nblk);
+  const int bps = (nblk + splits - 1) / splits;
+  if (splits > 1 && (!a.Ysplit || (a.D && !a.Dsplit))) return cudaErrorInvalidValue;
+  for (int sp = 0; sp < splits; ++sp)
+    for (int rt = 0; rt < row_tiles; ++rt)
+      for (int64_t c = 0; c < a.B; c += TC_BN_STD)
+        tiles.push_back(make_int4(rt, sp, (int)c, (int)std::min<int64_t>(c + TC_BN_STD, a.B)));
   TcParams p{};
-  p.nblk = a.nb_pow + (a.p_blk >= 0 ? 1 : 0);
+  p.nblk = nblk;
+  p.bps = splits > 1 ? bps : 0;
+  p.split_stride = a.B * a.N;
   p.grouped = 0;
   p.b0 = a.b0;
   p.nb_pow = a.nb_pow;
@@ -969,13 +1000,25 @@ cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
   p.coef = a.coef;
   p.coefd = a.coefd;
   p.ldcoef = a.B;
-  p.Y = a.Y;
-  p.D = a.D;
+  p.Y = splits > 1 && a.Y ? a.Ysplit : a.Y;
+  p.D = splits > 1 && a.D ? a.Dsplit : a.D;
   p.col_exp = a.col_exp;
   p.status = a.status;
   p.bimag = a.bimag;
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, 128, false, a.real_a, nullptr,
-                kc);
+  e = launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, 128, false, a.real_a, nullptr, kc);
+  if (e != cudaSuccess || splits == 1) return e;
+  if (a.Y && (e = fg_sum_splits(a.Ysplit, splits, a.B * a.N, a.Y, s)) != cudaSuccess) return e;
+  if (a.D) e = fg_sum_splits(a.Dsplit, splits, a.B * a.N, a.D, s);
+  return e;
+}
+
+int fg_tc_stacked_splits(int64_t N, int64_t B, int nblk) {
+  const int64_t tiles = ((N + TC_BM - 1) / TC_BM) * ((B + TC_BN_STD - 1) / TC_BN_STD);
+  const int64_t want = sm_count() / std::max<int64_t>(tiles, 1);
+  if (want < 2 || nblk < 2) return 1;
+  const int s0 = (int)std::min<int64_t>(want, nblk);
+  const int bps = (nblk + s0 - 1) / s0;
+  return (nblk + bps - 1) / bps;
 }
 
 cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {

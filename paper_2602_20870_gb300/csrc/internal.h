@@ -284,6 +284,8 @@ cudaError_t fg_simt_stacked(const SimtStackArgs& a, cudaStream_t s);
 cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* coef, float2* coefd, int64_t ldb,
                       int64_t ldj, cudaStream_t s);
 int fg_grad_chunks(int64_t N);
+// out = sum over s < splits of parts[s][0 .. count), float2 entries, in split order
+cudaError_t fg_sum_splits(const float2* parts, int splits, int64_t count, float2* out, cudaStream_t s);
 // out[j] = Re sum_i conj(G_ji) D_ji (FP64 partials per 1024-entry chunk, summed in a fixed
 // order); sum_all: out[0] = the sum over all j (one order shared by every column).
 cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N, float* out, double* partials,

@@ -2,6 +2,8 @@
 //  - per-column transform coefficients (Sec. III-A, Prop. 3) in FP64 on the device,
 //  - the alpha-gradient reduction g_j = Re sum_i conj(G_ij) D_ij (chain rule on Prop. 3),
 //  - the fp16 hi/lo split of signal columns for the tensor-core paths.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace {
@@ -367,7 +369,53 @@ cudaError_t fg_coeffs(const double* alpha, int B, int L, bool adjoint, float2* c
   return cudaGetLastError();
 }
 
+// out[i] = sum over s of parts[s * count + i], the splits in order (a fixed order, so the sum
+// is deterministic)
+__global__ void __launch_bounds__(256) sum_splits_kernel(const float4* __restrict__ parts, int splits, int64_t count4,
+                                                         float4* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count4; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 acc = parts[i];
+    for (int sp = 1; sp < splits; ++sp) {
+      const float4 v = parts[(int64_t)sp * count4 + i];
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+    out[i] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) sum_splits_tail_kernel(const float2* __restrict__ parts, int splits,
+                                                              int64_t count, int64_t from, float2* __restrict__ out) {
+  const int64_t i = from + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float2 acc = parts[i];
+  for (int sp = 1; sp < splits; ++sp) {
+    const float2 v = parts[(int64_t)sp * count + i];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  out[i] = acc;
+}
+
 int fg_grad_chunks(int64_t N) { return (int)((N + GR_CHUNK - 1) / GR_CHUNK); }
+
+cudaError_t fg_sum_splits(const float2* parts, int splits, int64_t count, float2* out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  // float4 pairs when every split starts 16-byte aligned (count even, 16-byte bases)
+  const bool vec = (count % 2 == 0) && ((uintptr_t)parts % 16 == 0) && ((uintptr_t)out % 16 == 0);
+  const int64_t done = vec ? count : 0;
+  if (vec) {
+    const int64_t c4 = count / 2;
+    const int64_t g = std::min<int64_t>((c4 + 255) / 256, 152 * 8);
+    sum_splits_kernel<<<(unsigned)g, 256, 0, s>>>((const float4*)parts, splits, c4, (float4*)out);
+  } else {
+    sum_splits_tail_kernel<<<(unsigned)((count - done + 255) / 256), 256, 0, s>>>(parts, splits, count, done, out);
+  }
+  fg_note_launch(FGFRFT_KC_TC_GEMM);
+  return cudaGetLastError();
+}
 
 cudaError_t fg_grad_alpha(const float2* G, const float2* D, int64_t B, int64_t N, float* out, double* partials,
                           cudaStream_t s, bool sum_all) {

@@ -64,8 +64,12 @@ struct TcStackedArgs {
   bool real_a;             // every stored block is real (real F)
   int* bimag;              // work: one word, 0 after the split when every signal is real
   bool x_real;             // X is real float32
+  float2* Ysplit;          // work: [splits][B][N] partial sums (splits > 1)
+  float2* Dsplit;          // work: the same for D
 };
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s);
+// Block splits of a stacked launch (1, or more when the tiles are fewer than the SMs).
+int fg_tc_stacked_splits(int64_t N, int64_t B, int nblk);
 
 // Fused multi-order assembly on the tensor cores: Q_a = sum_k C[a][k] S_k over all
 // stored blocks k (zero coefficients outside -L..L), from the entry-major split stack and
