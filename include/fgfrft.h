@@ -305,7 +305,8 @@ enum fgfrft_kernel_class {
 /* Process-wide instrumentation.  Launch counts are always kept.  While timing is
  * enabled, every call that launches kernels of a class records a CUDA event pair
  * around those launches on the call's stream (at most 65536 pairs per class
- * between resets).  fgfrft_timing_read synchronises on the recorded events and
+ * between resets).  Enabling creates a pool of 512 event pairs per class, so that timed
+ * calls only record events.  fgfrft_timing_read synchronises on the recorded events and
  * returns the launches, the timed calls and the summed device time in ms. */
 int fgfrft_timing_enable(int on);
 int fgfrft_timing_reset(void);

@@ -6,7 +6,8 @@
 
 namespace {
 
-constexpr size_t kMaxPairs = 1 << 16;  // recorded launches per class between resets
+constexpr size_t kMaxPairs = 1 << 16;        // recorded launches per class between resets
+constexpr size_t kPrecreatedPairs = 512;     // event pairs per class created when timing is enabled
 
 struct ClassLog {
   std::vector<cudaEvent_t> start, stop;  // event pool, reused after a reset
@@ -68,6 +69,22 @@ extern "C" {
 int fgfrft_timing_enable(int on) {
   std::lock_guard<std::mutex> g(T().mu);
   T().enabled = on != 0;
+  // create the event pool now, so that timed calls only record events (creating one inside
+  // a timed loop costs host time that would show up as gaps between launches)
+  if (on) {
+    for (auto& c : T().cls) {
+      while (c.start.size() < kPrecreatedPairs) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) break;
+        if (cudaEventCreate(&b) != cudaSuccess) {
+          cudaEventDestroy(a);
+          break;
+        }
+        c.start.push_back(a);
+        c.stop.push_back(b);
+      }
+    }
+  }
   return FGFRFT_OK;
 }
 
