@@ -844,7 +844,8 @@ def run_stacked(args):
                          "achieved": fl / (kms * 1e-3) / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                          "frac": fl / (kms * 1e-3) / 1e12 / tpeak, "algorithmic_flops": fl,
                          "executed_tensor_frac": 3 * fl / (kms * 1e-3) / 1e12 / tpeak,
-                         "peak_source": f"{src} bf16_tflops_sustained (fp16 dense rate equals bf16)"},
+                         "peak_source": f"{src} bf16_tflops_sustained (fp16 dense rate equals bf16)",
+                         "traffic": kernel_traffic("tc_gemm_kernel<128> (stacked)", "stacked")},
             "clocks": clocks}
     if not args.no_cpu_baseline:
         from oracle import fgfrft_oracle as O
