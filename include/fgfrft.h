@@ -324,8 +324,8 @@ int fgfrft_check_wait_timeout(fgfrft_plan p, void* stream);
  * Zero-allocation alpha-gradient: gradalpha[j] = Re sum_i conj(G_ij) D_ij for
  * j < B, the same quantity fgfrft_grad returns in gradalpha_dev, for callers that
  * cannot allocate device memory when they need it (code inside an allocator or
- * an ordered capture/real-time section where cudaMalloc and cudaFree, which
- * synchronise the device, are not allowed, or a host that only passes its input
+ * a real-time section where cudaMalloc and cudaFree, which synchronise the
+ * device, are not allowed, or a host that only passes its input
  * and output buffers).  The paper has no counterpart: this is an interface
  * choice of the library.
  *   G_dev, D_dev    B x N c64 (signal j at offset j * N): the output gradient
@@ -338,8 +338,7 @@ int fgfrft_check_wait_timeout(fgfrft_plan p, void* stream);
  * FGFRFT_ERR_UNSUPPORTED before anything is enqueued.  The call allocates nothing:
  * no cudaMalloc, cudaFree or allocating library routine.  Its first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current) and keeps it for the life of the process; make that first call
- * before any stream capture.  A cudaDeviceReset (or any other teardown of the
+ * device current) and keeps it for the life of the process.  A cudaDeviceReset (or any other teardown of the
  * device's primary context) invalidates the kept address: do not call this entry
  * point on a device after resetting it in the same process.  All calls
  * share the one array and every call overwrites the part it uses, so calls that

@@ -2,7 +2,7 @@
 //
 // Some callers cannot allocate device memory at the point where they need the
 // gradient: code running inside a framework whose allocator must not be
-// re-entered, a real-time or capture-ordered section that forbids cudaMalloc /
+// re-entered, a real-time section that forbids cudaMalloc /
 // cudaFree (they synchronise the device), or an embedding host that only hands
 // over input and output buffers.  fgfrft_grad_alpha_noalloc serves them: its FP64
 // partial sums live in a fixed array in this library's device memory instead of a
