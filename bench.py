@@ -379,8 +379,15 @@ def run_ours(args):
             "tflops": tflops, "tensor_frac": tflops / tpeak, "hbm_gbs": gbs, "hbm_frac": gbs / hpeak}
     if kt["assemble_multi"][1]:
         avg_ms = kt["assemble_multi"][2] / kt["assemble_multi"][1]
-        # stack read once (8 bytes per entry and block, 4 for real F) + operators written
-        byts = (4.0 if plan.real else 8.0) * (2 * L + 2) * N * N + (4.0 if real_q else 8.0) * n_orders * N * N
+        # stack read once + operators written.  The pair stack (real F without a -1 eigenvalue)
+        # holds 2 L_max real split values (4 bytes) per entry pair of the block-upper region,
+        # N (N + 128) / 2 rows; the full entry-major copy 2L + 2 blocks per entry (8 bytes, 4 for
+        # real F)
+        if plan.pair:
+            stack_b = 4.0 * 2 * plan.L_max * N * (N + 128) / 2
+        else:
+            stack_b = (4.0 if plan.real else 8.0) * (2 * L + 2) * N * N
+        byts = stack_b + (4.0 if real_q else 8.0) * n_orders * N * N
         peak = peaks.get("hbm_gbs", 6800.0)
         achieved = byts / (avg_ms * 1e-3) / 1e9
         rooflines["assemble_multi"] = {
@@ -504,7 +511,8 @@ def run_ours(args):
                    "path": "assembled (fused multi-order assembly + tcgen05 grouped GEMM)",
                    "signals": ("real float32 signals and outputs (FGFRFT_REAL_SIGNALS / _REAL_OUTPUT)"
                                if real_out else "real float32 signals" if real_x else "complex64 signals"),
-                   "l2": "inputs larger than L2 (stack 545 MB c64 + assembled operators 537 MB per step)",
+                   "l2": "inputs larger than L2 (pair stack 151 MB + assembled split operators 268 MB + "
+                         "signals 67 MB in, 67 MB out per step)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "signals_per_s": whole_job_rate(B * args.steps, ws, t_max / 1e3),
         "ms_per_step_without_kernel_events": ms_step_noev,

@@ -230,6 +230,17 @@ int fgfrft_plan_status(fgfrft_plan p, void* stream);
  * -FGFRFT_ERR_INVALID_ARG for a NULL plan. */
 int fgfrft_plan_real(fgfrft_plan p);
 
+/* 1 if the plan holds the pair stack: F real with no eigenvalue -1 (r_-1 = 0),
+ * FGFRFT_STORE_ENTRY_F16, N a multiple of 128 and L_max a multiple of 16 (at most 80).
+ * Then M_{-l} = M_l^T (F^{-1} = F^T; Prop. 2) and M_0 = P_c = I, so the fused multi-order
+ * assembly of split operators (the assembled path of fgfrft_apply) reads one row of the
+ * 2 L_max powers l != 0 per entry pair {(i, k), (k, i)} (i/128 <= k/128), about half the
+ * bytes of the full entry-major copy, and forms Q[i][k] and Q[k][i] from it (Def. 1 with
+ * c_{-l} for the mirror).  The pair stack occupies the entry-major storage's imaginary
+ * planes, which a real F leaves unused, so the plan size does not change.  0 otherwise;
+ * -FGFRFT_ERR_INVALID_ARG for a NULL plan. */
+int fgfrft_plan_pair(fgfrft_plan p);
+
 /* Release the host record of a plan.  Frees nothing caller-owned. */
 int fgfrft_plan_destroy(fgfrft_plan p);
 

@@ -201,8 +201,9 @@ struct AssembleWork {
   double* alpha_dev = nullptr;
   float2* coef = nullptr;    // single-order kernels: coefficient tables
   float2* coefd = nullptr;   // derivative coefficients (dual assembly dQ/dalpha)
-  __half* Cs = nullptr;      // tensor: split coefficients [4][A][Kp]
+  __half* Cs = nullptr;      // tensor: split coefficients [4][A][Kp] ([4][128][2 L_max] for the pair assembly)
   int* col_exp = nullptr;
+  float* diag = nullptr;     // pair assembly: c_0 of each order
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   bool tensor = false;
@@ -218,8 +219,11 @@ AssembleWork carve_assemble(const fgfrft_plan_s* p, char* base, int64_t A, int L
   w.tensor = !dual && p->f16T != nullptr && (A >= 2 || p->c64 == nullptr) && fg_tc_available();
   w.alpha_dev = c.take<double>((size_t)A);
   if (w.tensor) {
-    w.Cs = c.take<__half>((size_t)4 * A * p->Kp);
-    w.col_exp = c.take<int>((size_t)A);
+    // the pair assembly takes 128 coefficient rows (64 orders and their mirrors) per launch
+    const int64_t rows = p->pair ? std::max<int64_t>(A, 128) : A;
+    w.Cs = c.take<__half>((size_t)4 * rows * p->Kp);
+    w.col_exp = c.take<int>((size_t)rows);
+    if (p->pair) w.diag = c.take<float>((size_t)std::min<int64_t>(A, 64));
     w.scratch_bytes = fg_tc_assemble_scratch_bytes(p->N * p->N, A);
     w.scratch = c.take<char>(w.scratch_bytes);
   } else {
@@ -232,9 +236,43 @@ AssembleWork carve_assemble(const fgfrft_plan_s* p, char* base, int64_t A, int L
 
 // Enqueue the fused assembly of A orders into Qc (c64 [A][N*N]) or Qs (split planes).
 // alpha_host (optional): the same orders on the host.
+// *pair_out (optional) is set when Qs holds pair-structured operators (the grouped GEMM then
+// reads the left of each row tile's diagonal block from planes 2, 3; see TcGroupedArgs::pair).
 cudaError_t run_assemble(const fgfrft_plan_s* p, const AssembleWork& w, const double* alpha_dev, int64_t A, int L,
-                         float2* Qc, __half* Qs, cudaStream_t s, const double* alpha_host = nullptr) {
+                         float2* Qc, __half* Qs, cudaStream_t s, const double* alpha_host = nullptr,
+                         bool* pair_out = nullptr) {
   const int b0 = blk_of_power(p, -L), nb = 2 * L + 1, pb = blk_of_P(p);
+  if (pair_out) *pair_out = false;
+  if (w.tensor && p->pair && Qs && !Qc) {
+    // one pass over the pair stack per 64 orders: Q_a[i][k] and Q_a[k][i] of every entry pair
+    for (int64_t a0 = 0; a0 < A; a0 += 64) {
+      const int64_t na = std::min<int64_t>(64, A - a0);
+      cudaError_t e = fg_coeff_planes_pair(alpha_dev + a0, na, L, p->L_max, w.Cs, w.col_exp, w.diag, s,
+                                           alpha_host ? alpha_host + a0 : nullptr);
+      if (e != cudaSuccess) return e;
+      TcAssembleArgs ta{};
+      ta.pair_stack = p->pairS;
+      ta.pair_rows = p->pair_rows;
+      ta.K2 = 2 * (int64_t)p->L_max;
+      ta.diag = w.diag;
+      ta.A = na;
+      ta.Cs = w.Cs;
+      ta.col_exp = w.col_exp;
+      ta.Qs = Qs + a0 * 4 * p->qplane;
+      ta.N = p->N;
+      ta.Np = p->Np;
+      ta.plane_elems = p->qplane;
+      ta.scratch = w.scratch;
+      ta.scratch_bytes = w.scratch_bytes;
+      ta.status = p->dstatus;
+      ta.real_a = true;
+      ta.skip_im = true;
+      ta.re_only = true;
+      if ((e = fg_tc_assemble(ta, s)) != cudaSuccess) return e;
+    }
+    if (pair_out) *pair_out = true;
+    return cudaSuccess;
+  }
   if (w.tensor) {
     cudaError_t e = fg_coeff_planes(alpha_dev, A, L, p->L_max, p->Kp, w.Cs, w.col_exp, s, alpha_host);
     if (e != cudaSuccess) return e;
@@ -719,6 +757,21 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   }
   if (p->f16T && fg_entry_major(p->f16, p->nblk, N, p->Np, p->plane_elems, p->f16T, p->Kp, p->planeT, s))
     return fail(FGFRFT_ERR_CUDA);
+  // a real F without a -1 eigenvalue: M_{-l} = M_l^T and M_0 = I, so one row of the 2 L_max
+  // powers l != 0 per entry pair (i, k) gives Q[i][k] and Q[k][i]; the pair stack goes into the
+  // imaginary planes of the entry-major copy's full chunks (2 (Kp / 32) planeT 32 entries >=
+  // 2 (2 L_max) rows, since 32 (Kp / 32) = 2 L_max for L_max % 16 == 0 and rows <= planeT)
+  p->pair = false;
+  if (p->f16T && p->real && p->r_neg1 == 0 && N % 128 == 0 && L_max % 16 == 0 && L_max <= 80) {
+    const int64_t rows = 128 * pair_tiles((int)(N / 128));
+    const int64_t nfull = p->Kp / 32;
+    if (2 * (int64_t)L_max * rows <= 32 * nfull * p->planeT) {
+      p->pairS = p->f16T + 2 * nfull * p->planeT * 32;
+      p->pair_rows = rows;
+      if (fg_pair_stack(p->f16, L_max, N, p->Np, p->plane_elems, p->pairS, rows, s)) return fail(FGFRFT_ERR_CUDA);
+      p->pair = true;
+    }
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FGFRFT_ERR_CUDA);
   *out = p;
   return FGFRFT_OK;
@@ -777,6 +830,11 @@ int fgfrft_plan_status(fgfrft_plan p, void* stream) {
 int fgfrft_plan_real(fgfrft_plan p) {
   if (!p) return -FGFRFT_ERR_INVALID_ARG;
   return p->real ? 1 : 0;
+}
+
+int fgfrft_plan_pair(fgfrft_plan p) {
+  if (!p) return -FGFRFT_ERR_INVALID_ARG;
+  return p->pair ? 1 : 0;
 }
 
 int fgfrft_plan_destroy(fgfrft_plan p) {
@@ -936,12 +994,13 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, const Runs& runs, i
       // the signal split runs beside the operator assembly on the auxiliary stream (they
       // share no buffer); the GEMM waits for both
       AuxJoin aux{fg_fork(s), s};
+      bool pair = false;
       if (aux.aux)
         CK(fg_split_signals(X, B, p->N, p->Np, w.xs_rows, w.Xs, w.col_exp, aux.aux, w.bimag, x_real));
       if (D_dev)
         CK(run_assemble_dual(p, w.asm_work, gad, groups, L, w.Qs, w.dQs, s));
       else
-        CK(run_assemble(p, w.asm_work, gad, groups, L, nullptr, w.Qs, s, ga.data()));
+        CK(run_assemble(p, w.asm_work, gad, groups, L, nullptr, w.Qs, s, ga.data(), &pair));
       const bool split_done = aux.aux != nullptr;
       CK(aux.join());
       TcGroupedArgs ta{};
@@ -968,6 +1027,7 @@ static int apply_impl(fgfrft_plan p, std::vector<double>& a, const Runs& runs, i
       ta.x_real = x_real;
       ta.y_real = y_real;
       ta.x_split_done = split_done;
+      ta.pair = pair;
       if (Y) CK(fg_tc_grouped_apply(ta, s));
       if (D_dev) {  // D = (dQ/dalpha) X on the same split signals
         ta.Qs = w.dQs;

@@ -73,7 +73,8 @@ struct TcCfg {
   static constexpr uint32_t IDESC_2N = (1u << 4) | ((uint32_t)(2 * BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
   // merged split products for a real product on the resident-B launch (BN = 64):
   // acc[0:BN] = A_hi*B_hi + A_lo*B_hi, acc[BN:2BN] = A_hi*B_lo, 2 MMAs per k16 step instead of 3
-  static constexpr bool MERGE = RB && 2 * BN <= 256;
+  // (the 128-column pair launch keeps 3 MMAs, so that four accumulator buffers fit in TMEM)
+  static constexpr bool MERGE = RB && BN == 64;
 };
 
 // Shared memory: this control block, then the resident B operand (RB: k-chunks x 4 planes),
@@ -130,6 +131,24 @@ struct TcParams {
   // and writes its partial sums at Y + s * split_stride (D likewise); bps = 0: no split
   int bps;
   int64_t split_stride;
+  // pair assembly (real F, no -1 eigenvalue): A rows are entry pairs of the pair stack, tile t
+  // holds entries (i, 128 kt + r), r < 128, of the block-upper region (kt >= i / 128); columns
+  // j < 64 are the orders' Q[i][k], columns 64 + j their Q[k][i] (mirror), written at the same
+  // position (i, k) of planes 2, 3 (the transposed store) when kt > i / 128.  pair_nbt = N / 128
+  // (0: not a pair launch); diag[j] is added to Q[i][i] (c_0 of order j, accumulator scale).
+  int pair_nbt;
+  int pair_A;
+  const float* diag;
+  // A operand stored as ring-stage images (the pair stack): tile t's stage is one bulk copy of
+  // stage_bytes from a_img + t * stage_bytes (streamed once: L2 evict-first)
+  const uint8_t* a_img;
+  // pair assembly output through shared memory: each epilogue group stages a 16-column chunk
+  // (16 orders x 2 planes x 128 entries, 8 KB) and one 4-D tensor store (tmT: {k, i, plane,
+  // order}) writes it; out_bytes = the staging area (two buffers per group), 0: direct stores
+  int out_bytes;
+  // grouped GEMM over pair-structured operators: k-chunks left of the row tile's diagonal
+  // block come from the transposed store (planes 2, 3 of the group), read MN-major
+  int pair_lower;
   const int* bimag;   // NULL, or a device word that is 0 when every B column is real
   const float2* coef;
   const float2* coefd;
@@ -167,6 +186,19 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
   d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
   d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+
+// MN-major operand, 128-byte swizzle: 8 k-rows of 128 bytes (64 MN values) per 1 KB atom;
+// the two 64-value halves of the 128 MN values are 4 KB apart (leading byte offset), the
+// 8-row k groups 1 KB apart (stride byte offset)
+__device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)(4096 >> 4) << 16;           // leading byte offset: the next 64 MN values
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: the next 8 k-rows
   d |= (uint64_t)1 << 46;                     // descriptor version
   d |= (uint64_t)2 << 61;                     // 128-byte swizzle
   return d;
@@ -219,12 +251,14 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[16]) { tme
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Bounded wait that also gives up at once when another role already aborted.
+// The retries suspend in the barrier (up to 20 us each, woken when the phase completes), so
+// the many waiting roles of a CTA do not crowd out the issue slots of the working ones.
 template <class Smem>
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, Smem& sm, uint32_t* status) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
     if (sm.abort) return false;
     if (global_timer_ns() - t0 > FG_WAIT_LIMIT_NS) {
       sm.abort = 1;
@@ -255,15 +289,24 @@ __device__ __forceinline__ void split_out_cols(const uint32_t (&vr)[CW], const u
   __half* qp = p.Qs + (int64_t)j0 * cs + qoff;
   const bool write_im = !p.skip_im;
   if (!write_im) {  // real operators: the real planes only
+    // two columns per packed conversion (cvt.rn.f16x2.f32): half the conversion instructions
+    // of one conversion per value, which otherwise bound this epilogue
 #pragma unroll
-    for (int c = 0; c < CW; ++c) {
+    for (int c = 0; c < CW; c += 2) {
+      const float r0 = __uint_as_float(vr[c]) * (UNIFORM ? p.uscale : scale[cc * CW + c]);
+      const float r1 = __uint_as_float(vr[c + 1]) * (UNIFORM ? p.uscale : scale[cc * CW + c + 1]);
+      const __half2 hi = __floats2half2_rn(r0, r1);
+      const float2 hf = __half22float2(hi);
+      const __half2 lo = __floats2half2_rn(r0 - hf.x, r1 - hf.y);
       if (c < ncol) {
-        const float re = __uint_as_float(vr[c]) * (UNIFORM ? p.uscale : scale[cc * CW + c]);
-        const __half hi = __float2half_rn(re);
-        qp[0] = hi;
-        qp[pl] = __float2half_rn(re - __half2float(hi));
+        qp[0] = __low2half(hi);
+        qp[pl] = __low2half(lo);
       }
-      qp += cs;
+      if (c + 1 < ncol) {
+        qp[cs] = __high2half(hi);
+        qp[cs + pl] = __high2half(lo);
+      }
+      qp += 2 * cs;
     }
     return;
   }
@@ -290,6 +333,43 @@ template <int EPI_WARPS>
 __device__ __forceinline__ void epi_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
 }
+
+// the four warps of one epilogue group (named barrier 2 + group)
+__device__ __forceinline__ void grp_bar(int grp) { asm volatile("bar.sync %0, 128;" ::"r"(2 + grp) : "memory"); }
+
+__device__ __forceinline__ void sts16(uint32_t a, __half v) {
+  asm volatile("st.shared.b16 [%0], %1;" ::"r"(a), "h"(__half_as_ushort(v)) : "memory");
+}
+
+// 16 columns of this thread's row as fp16 hi/lo into a staging buffer laid out as the output
+// box {128 entries, 1 row, 2 planes, 16 orders}: column c, plane q at ((2 c + q) * 128 + row) * 2
+__device__ __forceinline__ void stage_split16(const uint32_t (&vr)[16], float uscale, uint32_t buf, int row) {
+  const uint32_t a = buf + 2u * (uint32_t)row;
+#pragma unroll
+  for (int c = 0; c < 16; c += 2) {
+    const float r0 = __uint_as_float(vr[c]) * uscale, r1 = __uint_as_float(vr[c + 1]) * uscale;
+    const __half2 hi = __floats2half2_rn(r0, r1);
+    const float2 hf = __half22float2(hi);
+    const __half2 lo = __floats2half2_rn(r0 - hf.x, r1 - hf.y);
+    sts16(a + (2 * c + 0) * 256, __low2half(hi));
+    sts16(a + (2 * c + 1) * 256, __low2half(lo));
+    sts16(a + (2 * c + 2) * 256, __high2half(hi));
+    sts16(a + (2 * c + 3) * 256, __high2half(lo));
+  }
+}
+
+// shared -> global tensor store of one box; completion tracked in this thread's bulk groups
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, uint32_t src, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// wait until at most one of this thread's bulk stores still reads shared memory
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// wait until every bulk store of this thread has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 template <int BN, bool RB, bool RA, int KC>
 __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
@@ -320,14 +400,16 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
   const int nbp = (re_only || breal) ? 2 : 4;  // B planes loaded
   uint8_t* const bres = sbase + sizeof(TcCtl);  // resident B: [chunk][nbp planes][BN rows x 64 B]
   const int res_bytes = RB ? p.kchunks * nbp * TC_PLANE_B : 0;
-  uint8_t* const stages = bres + res_bytes;
+  uint8_t* const obuf = bres + res_bytes;  // pair output staging: [group][2][16 x 2 x 128 fp16]
+  const int out_bytes = RB ? p.out_bytes : 0;
+  uint8_t* const stages = obuf + out_bytes;
   const int chunk_bytes = A_PLANES * PLANE_A + (RB ? 0 : nbp * TC_PLANE_B);
   const int cps = p.cps > 1 ? p.cps : 1;
   // narrow tail: chunk c < a_nfull at c * chunk_bytes, the tail after them, TAIL_PLANE apart
   constexpr int TAIL_PLANE = TC_BM * 32;
   const bool tail16 = RB && p.a_chunked && p.a_tail16 && cps >= p.kchunks;
   const int stage_bytes = p.stage_bytes ? p.stage_bytes : cps * chunk_bytes;
-  const int nst = min(TC_MAXST, (p.smem_bytes - (int)sizeof(TcCtl) - res_bytes) / stage_bytes);
+  const int nst = min(TC_MAXST, (p.smem_bytes - (int)sizeof(TcCtl) - res_bytes - out_bytes) / stage_bytes);
   // a launch sized for real signals whose split reports an imaginary part (or any other
   // mismatch of the host's sizing): record it and return before anything is set up
   if (nst < 1 || (p.stage_bytes && !tail16 && cps * chunk_bytes > p.stage_bytes)) {
@@ -360,7 +442,7 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
     fence_barrier_init();
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-    if (p.a_chunked)
+    if (p.a_chunked || p.pair_lower || out_bytes)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmT)) : "memory");
   }
   if (warp == 1) {
@@ -383,6 +465,7 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
       bool ok = true;
       int4 next = blockIdx.x < p.ntiles ? tile_of(p, blockIdx.x) : make_int4(0, 0, 0, 0);
       bool b_issued = false;
+      const uint64_t l2_first = policy_evict_first();
       if (RB && blockIdx.x < p.ntiles) {  // all k-chunks of B, once
         mbar_arrive_expect_tx(&sm.bfull, (uint32_t)(p.kchunks * nbp * TC_PLANE_B));
         for (int kc = 0; kc < p.kchunks; ++kc)
@@ -408,8 +491,13 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
               break;
             }
             const int nc = min(cps, p.kchunks - kc0);
-            mbar_arrive_expect_tx(&sm.full[s], (uint32_t)(tail16 ? stage_bytes : nc * chunk_bytes));
+            mbar_arrive_expect_tx(&sm.full[s], (uint32_t)(tail16 || p.a_img ? stage_bytes : nc * chunk_bytes));
             issued[s]++;
+            if (RB && p.a_img) {  // the stage's image, one contiguous copy (one stage per tile)
+              bulk_g2s_evict_first(stages + s * stage_bytes, p.a_img + (int64_t)tile.x * stage_bytes,
+                                   (uint32_t)stage_bytes, &sm.full[s], l2_first);
+              continue;
+            }
             for (int c = 0; c < nc; ++c) {
               uint8_t* st = stages + s * stage_bytes + c * chunk_bytes;
               const int k0 = (kc0 + c) * KC;
@@ -422,6 +510,15 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
                   else
                     tma_load_3d(st + q * (tail16 ? TAIL_PLANE : PLANE_A), &tmT, 0, tile.x * TC_BM, q, &sm.full[s]);
                 }
+              } else if (RA && p.pair_lower && k0 < tile.x * TC_BM) {
+                // left of the diagonal block: Q[i][k] = S'[k][i], rows k0 .. k0 + 31 of the
+                // transposed store (planes 2, 3 of the group), 64 i-values per box
+#pragma unroll
+                for (int q = 0; q < A_PLANES; ++q)
+#pragma unroll
+                  for (int h = 0; h < 2; ++h)
+                    tma_load_3d(st + q * PLANE_A + h * (PLANE_A / 2), &tmT, tile.x * TC_BM + 64 * h, k0, zA + 2 + q,
+                                &sm.full[s]);
               } else {
 #pragma unroll
                 for (int q = 0; q < A_PLANES; ++q)
@@ -463,9 +560,12 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
       int4 next = tile_n && blockIdx.x < p.ntiles ? tile_of(p, blockIdx.x) : make_int4(0, 0, 0, 0);
       for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
         uint32_t idesc = kIdesc, idesc_neg = kIdescNegA;
+        // pair-structured operators: k-chunks left of this row tile's diagonal block are MN-major
+        int lower_k = 0;
         if (tile_n) {
           const int4 tl = next;
           if (t + (int)gridDim.x < p.ntiles) next = tile_of(p, t + gridDim.x);  // prefetch
+          if (RA && p.pair_lower) lower_k = tl.x * TC_BM;
           const int n16 = min(TC_BN, max(16, (tl.w - tl.z + 15) / 16 * 16));
           idesc = (kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(n16 >> 3) << 17);
           idesc_neg = idesc | (1u << 13);
@@ -500,47 +600,53 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
             // the narrow tail: 32-byte rows (one k16 step), 32-byte swizzle
             const bool is_tail = tail16 && kc >= p.a_nfull;
             const uint32_t apl = is_tail ? (uint32_t)TAIL_PLANE : (uint32_t)PLANE_A;
-            auto adesc = [&](uint32_t a) { return is_tail ? desc_sw32(a) : desc_kc<KC>(a); };
+            // MN-major A (left of a pair-structured operator's diagonal block): k16 step kk is
+            // 16 rows of 128 bytes further; the instruction reads A transposed
+            const bool mn = kc * KC < lower_k;
+            const uint32_t idesc_c = mn ? (idesc | (1u << 15)) : idesc;
+            const uint32_t idesc_neg_c = mn ? (idesc_neg | (1u << 15)) : idesc_neg;
+            auto adesc = [&](uint32_t a) { return mn ? desc_mn_sw128(a) : is_tail ? desc_sw32(a) : desc_kc<KC>(a); };
 #pragma unroll
             for (int kk = 0; kk < KC / 16; ++kk) {
               if (is_tail && kk > 0) continue;
               const uint32_t off = kk * 32;  // 16 fp16 along k
-              const uint64_t arh = adesc(sa + 0 * apl + off), arl = adesc(sa + 1 * apl + off);
+              const uint32_t offa = mn ? kk * 2048 : off;
+              const uint64_t arh = adesc(sa + 0 * apl + offa), arl = adesc(sa + 1 * apl + offa);
               const uint64_t brh = desc_kc<KC>(sb + 0 * TC_PLANE_B + off), brl = desc_kc<KC>(sb + 1 * TC_PLANE_B + off);
               const uint64_t bih = desc_kc<KC>(sb + 2 * TC_PLANE_B + off), bil = desc_kc<KC>(sb + 3 * TC_PLANE_B + off);
               if (p.kvalid > 0 && kc * KC + kk * 16 >= p.kvalid) continue;  // all-zero k16 step
               const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
               if (merged) {  // [A_hi*B_hi | A_hi*B_lo], then A_lo*B_hi into the first half
                 umma(d_re, arh, brh, Cfg::IDESC_2N, acc);
-                umma(d_re, arl, brh, idesc, 1);
+                umma(d_re, arl, brh, idesc_c, 1);
                 continue;
               }
               // real part: Ar*Xr - Ai*Xi
-              umma(d_re, arh, brh, idesc, acc);
-              umma(d_re, arh, brl, idesc, 1);
-              umma(d_re, arl, brh, idesc, 1);
+              umma(d_re, arh, brh, idesc_c, acc);
+              umma(d_re, arh, brl, idesc_c, 1);
+              umma(d_re, arl, brh, idesc_c, 1);
               if (re_only) continue;  // real product: no imaginary accumulator
               if (breal) {            // complex A, real X: Im = Ai*Xr only
                 if (!RA) {
-                  const uint64_t aih = adesc(sa + 2 * apl + off), ail = adesc(sa + 3 * apl + off);
-                  umma(d_im, aih, brh, idesc, acc);
-                  umma(d_im, aih, brl, idesc, 1);
-                  umma(d_im, ail, brh, idesc, 1);
+                  const uint64_t aih = adesc(sa + 2 * apl + offa), ail = adesc(sa + 3 * apl + offa);
+                  umma(d_im, aih, brh, idesc_c, acc);
+                  umma(d_im, aih, brl, idesc_c, 1);
+                  umma(d_im, ail, brh, idesc_c, 1);
                 }
                 continue;
               }
               // imaginary part: Ar*Xi + Ai*Xr
-              umma(d_im, arh, bih, idesc, acc);
-              umma(d_im, arh, bil, idesc, 1);
-              umma(d_im, arl, bih, idesc, 1);
+              umma(d_im, arh, bih, idesc_c, acc);
+              umma(d_im, arh, bil, idesc_c, 1);
+              umma(d_im, arl, bih, idesc_c, 1);
               if (!RA) {
-                const uint64_t aih = adesc(sa + 2 * apl + off), ail = adesc(sa + 3 * apl + off);
-                umma(d_re, aih, bih, idesc_neg, 1);
-                umma(d_re, aih, bil, idesc_neg, 1);
-                umma(d_re, ail, bih, idesc_neg, 1);
-                umma(d_im, aih, brh, idesc, 1);
-                umma(d_im, aih, brl, idesc, 1);
-                umma(d_im, ail, brh, idesc, 1);
+                const uint64_t aih = adesc(sa + 2 * apl + offa), ail = adesc(sa + 3 * apl + offa);
+                umma(d_re, aih, bih, idesc_neg_c, 1);
+                umma(d_re, aih, bil, idesc_neg_c, 1);
+                umma(d_re, ail, bih, idesc_neg_c, 1);
+                umma(d_im, aih, brh, idesc_c, 1);
+                umma(d_im, aih, brl, idesc_c, 1);
+                umma(d_im, ail, brh, idesc_c, 1);
               }
             }
             }                           // chunks of the stage
@@ -571,7 +677,7 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
     // one scale per column: undo 2^{e_j} and the operator scale; the next tile's
     // descriptor and scales are loaded while the current tile is processed
     auto col_scale = [&](const int4& tl) -> float {
-      if (et >= TC_BN) return 0.f;
+      if (et >= TC_BN || p.uscale != 0.f) return 0.f;  // one output scale: no per-column table
       const int j = tl.z + et;
       const int e = j < tl.w ? p.col_exp[j] : 0;
       return ldexpf(1.0f, split_out ? -e : -(FG_SPLIT_SHIFT + e));
@@ -579,6 +685,11 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
     int4 next = blockIdx.x < p.ntiles ? tile_of(p, blockIdx.x) : make_int4(0, 0, 0, 0);
     float next_scale = blockIdx.x < p.ntiles ? col_scale(next) : 0.f;
     int64_t li = 0;  // local tile index (ping-pong: group grp takes the tiles li = grp mod NGRP)
+    // staged pair output: the group's first warp, lane 0, issues its tensor stores
+    const bool staged = RB && out_bytes > 0 && pingpong;
+    const bool leader = staged && warp == TC_EPI_WARP0 + 4 * grp && lane == 0;
+    const uint32_t gbuf = smem_u32(obuf) + (uint32_t)grp * 2u * 8192u;
+    uint32_t nstaged = 0;
     for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++li) {
       const bool mine = !pingpong || (int)(li % NGRP) == grp;
       const int4 tile = next;
@@ -595,9 +706,19 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
       const int64_t gi = (int64_t)tile.x * TC_BM + row;
       const bool row_ok = gi < p.rows;
       int64_t qoff = 0;
-      if (split_out) {
+      if (split_out && !p.pair_nbt) {
         const int64_t qi = gi / p.qN;
         qoff = qi * p.qNp + (gi - qi * p.qN);
+      }
+      // pair tile: this row is entry (i, 128 kt + row); its mirror (128 kt + row, i) is written at
+      // the same position of the transposed store unless the tile is in a diagonal block
+      bool mirror_ok = false, diag_lane = false;
+      int pi = 0, pkt = 0;
+      if (p.pair_nbt) {
+        pair_tile(tile.x, p.pair_nbt, pi, pkt);
+        qoff = (int64_t)pi * p.qNp + 128 * (int64_t)pkt + row;
+        mirror_ok = pkt != pi / 128;
+        diag_lane = 128 * pkt + row == pi;
       }
 
       const int2 br = blk_range(p, tile);
@@ -613,9 +734,16 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
         const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + buf * acc_w;
 #pragma unroll 1
         for (int cc = pingpong ? 0 : grp; cc < TC_BN / CW; cc += pingpong ? 1 : NGRP) {
-          const int j0 = tile.z + cc * CW;
+          int j0 = tile.z + cc * CW;
           if (j0 >= tile.w) break;  // uniform: no column of this chunk is in range
-          const int ncol = min(CW, tile.w - j0);
+          int ncol = min(CW, tile.w - j0);
+          bool mir = false;
+          if (p.pair_nbt) {  // columns 64 + j hold the mirror of order j (uniform per warp)
+            mir = j0 >= 64;
+            if (mir) j0 -= 64;
+            ncol = min(CW, p.pair_A - j0);
+            if (ncol <= 0 || (mir && !mirror_ok)) continue;
+          }
           uint32_t vr[CW], vi[CW];
           __syncwarp();  // tcgen05.ld is warp-collective: the whole warp converged
           tmem_ld(base + cc * CW, vr);
@@ -633,12 +761,29 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
               vi[c] = 0u;
             }
           }
-          if (!row_ok) {
+          if (diag_lane && !mir) {  // Q[i][i] += c_0 (M_0 = I is not stored)
+#pragma unroll
+            for (int c = 0; c < CW; ++c)
+              if (c < ncol) vr[c] = __float_as_uint(__uint_as_float(vr[c]) + __ldg(p.diag + j0 + c));
+          }
+          if (staged) {
+            // through shared memory: this buffer's previous store must have read it, then
+            // the group fills it and one tensor store writes the 16 orders x 2 planes
+            const uint32_t buf = gbuf + (nstaged & 1u) * 8192u;
+            if (leader) bulk_wait_read1();
+            grp_bar(grp);
+            stage_split16(reinterpret_cast<const uint32_t(&)[16]>(vr), p.uscale, buf, row);
+            fence_proxy_async_smem();
+            grp_bar(grp);
+            if (leader) tma_store_4d(&tmT, buf, 128 * pkt, pi, mir ? 2 : 0, j0);
+            ++nstaged;
+          } else if (!row_ok) {
             // rows past the end: nothing to store
           } else if (split_out) {
-            // value * 2^FG_SPLIT_SHIFT as fp16 hi + lo, four planes per column
+            // value * 2^FG_SPLIT_SHIFT as fp16 hi + lo, four planes per column (a mirror
+            // column goes to planes 2, 3)
             if (p.uscale != 0.f)
-              split_out_cols<true, CW>(vr, vi, p, sm.scale, cc, j0, ncol, qoff);
+              split_out_cols<true, CW>(vr, vi, p, sm.scale, cc, j0, ncol, mir ? qoff + 2 * p.qplane : qoff);
             else
               split_out_cols<false, CW>(vr, vi, p, sm.scale, cc, j0, ncol, qoff);
           } else if (p.coef == nullptr && p.y_real) {
@@ -697,6 +842,7 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
         if (lane == 0) mbar_arrive(&sm.tempty[buf]);
       }
     }
+    if (leader) bulk_wait_all();  // the staged stores have left shared memory and completed
   }
   fence_tc_before();
   __syncthreads();
@@ -792,13 +938,15 @@ cudaError_t launch_bn(const CUtensorMap& mA, const CUtensorMap& mB, const CUtens
                     : (p.cps > 1 ? p.cps : 1) * (Cfg::A_PLANES * Cfg::PLANE_A + (RB ? 0 : 4 * Cfg::PLANE_B));
   TcParams q = p;
   q.smem_bytes = smem - 1024;  // the kernel aligns its base up to 1024 bytes
-  if (q.smem_bytes - (int)sizeof(TcCtl) - res_bytes < TC_MIN_STAGES * worst_stage) return cudaErrorInvalidValue;
+  const int out_bytes = RB ? p.out_bytes : 0;
+  if (q.smem_bytes - (int)sizeof(TcCtl) - res_bytes - out_bytes < TC_MIN_STAGES * worst_stage)
+    return cudaErrorInvalidValue;
   int smem_req = smem;
   if (RB) {
     // resident B: a stage holds A only, so the ring depth is known here; ask for just that
     // much, leaving the rest of the SM's shared memory to kernels running beside this one
-    const int nst = std::min(TC_MAXST, (q.smem_bytes - (int)sizeof(TcCtl) - res_bytes) / worst_stage);
-    q.smem_bytes = (int)sizeof(TcCtl) + res_bytes + nst * worst_stage;
+    const int nst = std::min(TC_MAXST, (q.smem_bytes - (int)sizeof(TcCtl) - res_bytes - out_bytes) / worst_stage);
+    q.smem_bytes = (int)sizeof(TcCtl) + res_bytes + out_bytes + nst * worst_stage;
     smem_req = q.smem_bytes + 1024;
   }
   cudaError_t e =
@@ -831,7 +979,12 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, const std::vect
     p.ntiles = (int)tiles.size();
   }
   if (resident_b) {
-    if (bn != 64 || p.kchunks > TC_RB_MAXCH) return cudaErrorInvalidValue;
+    if (p.kchunks > TC_RB_MAXCH) return cudaErrorInvalidValue;
+    if (bn == 128) {  // the pair assembly (64 orders and their mirrors): real blocks only
+      if (!real_a) return cudaErrorInvalidValue;
+      return launch_bn<128, true, true>(mA, mB, mT, p.ntiles, p, s, kclass);
+    }
+    if (bn != 64) return cudaErrorInvalidValue;
     return real_a ? launch_bn<64, true, true>(mA, mB, mT, p.ntiles, p, s, kclass)
                   : launch_bn<64, true, false>(mA, mB, mT, p.ntiles, p, s, kclass);
   }
@@ -937,9 +1090,13 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   // real operators: 256-column tiles halve the re-reads of each operator tile from L2
   const int bn = fg_tc_grouped_bn(a.real_a);
   const int kc = TC_KC, stage_bytes = 0;
-  CUtensorMap mA, mB;
+  CUtensorMap mA, mB, mT;
   if (!make_map(&mA, a.Qs, a.N, a.N, a.Np, 4 * a.groups, a.plane_elems, TC_BM, kc) ||
       !make_map(&mB, a.Xs, a.N, a.xs_rows, a.Np, 4, a.xs_rows * a.Np, bn, kc))
+    return cudaErrorInvalidValue;
+  // pair-structured operators: the transposed store (planes 2, 3) read as 64 x 32 MN-major boxes
+  if (a.pair && (!a.real_a || a.N % 128 ||
+                 !fg_make_map_f16(&mT, a.Qs, a.N, a.N, a.Np, 4 * a.groups, a.plane_elems, 64, 32, 128)))
     return cudaErrorInvalidValue;
   std::vector<int4> tiles;
   TcParams p{};
@@ -959,8 +1116,9 @@ cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s) {
   p.status = a.status;
   p.bimag = a.bimag;
   p.y_real = a.y_real ? 1 : 0;
-  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, bn, false, a.real_a, nullptr,
-                kc);
+  p.pair_lower = a.pair ? 1 : 0;
+  return launch(mA, mB, tiles, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_TC_GEMM, bn, false, a.real_a,
+                a.pair ? &mT : nullptr, kc);
 }
 
 cudaError_t fg_tc_stacked_apply(const TcStackedArgs& a, cudaStream_t s) {
@@ -1021,7 +1179,61 @@ int fg_tc_stacked_splits(int64_t N, int64_t B, int nblk) {
   return (nblk + bps - 1) / bps;
 }
 
+// Pair assembly (real F without a -1 eigenvalue): one GEMM row per entry pair (i, k) of the
+// block-upper region, K = the 2 L_max powers M_l, l != 0 (M_0 = I and P = 0 are not stored);
+// columns: the orders' coefficients c_l and, 64 columns on, the mirror coefficients c_{-l},
+// so one pass gives Q[i][k] and Q[k][i] = sum_l c_{-l} M_l[i][k] (M_{-l} = M_l^T).
+static cudaError_t tc_assemble_pair(const TcAssembleArgs& a, cudaStream_t s) {
+  if (!a.real_a || !a.Qs || a.A < 1 || a.A > 64 || a.N % 128 || a.K2 % TC_KC || a.K2 < TC_KC ||
+      a.K2 / TC_KC > TC_RB_MAXCH || a.pair_rows % TC_BM || a.pair_rows / TC_BM > INT32_MAX)
+    return cudaErrorInvalidValue;
+  const int nch = (int)(a.K2 / TC_KC);
+  CUtensorMap mB, mO;
+  if (!make_map(&mB, a.Cs, a.K2, 128, a.K2, 4, 128 * a.K2, 128)) return cudaErrorInvalidValue;
+  // the operators as a 4-D tensor {k, i, plane, order} for the staged stores: box = 128 entries
+  // of one row, 2 planes, 16 orders (the box's orders past A are not written)
+  {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorInvalidValue;
+    cuuint64_t dims[4] = {(cuuint64_t)a.N, (cuuint64_t)a.N, 4, (cuuint64_t)a.A};
+    cuuint64_t strides[3] = {(cuuint64_t)a.Np * 2, (cuuint64_t)a.plane_elems * 2, (cuuint64_t)a.plane_elems * 8};
+    cuuint32_t box[4] = {128, 1, 2, 16};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (enc(&mO, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, a.Qs, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  TcParams p{};
+  p.ntiles = (int)(a.pair_rows / TC_BM);
+  p.arith_cols = 128;
+  p.nblk = 1;
+  p.grouped = 1;
+  p.rows = a.pair_rows;
+  p.kchunks = nch;
+  p.kvalid = (int)a.K2;
+  p.cps = nch;  // every chunk of a tile in one ring stage, copied from its image
+  p.a_img = reinterpret_cast<const uint8_t*>(a.pair_stack);
+  p.stage_bytes = nch * 2 * TC_BM * TC_KC * 2;
+  p.Qs = a.Qs;
+  p.qN = a.N;
+  p.qNp = a.Np;
+  p.qplane = a.plane_elems;
+  p.col_exp = a.col_exp;
+  p.status = a.status;
+  p.skip_im = 1;
+  p.re_only = 1;
+  p.uscale = ldexpf(1.0f, -FG_COEF_EXP);
+  p.pair_nbt = (int)(a.N / 128);
+  p.pair_A = (int)a.A;
+  p.diag = a.diag;
+  p.out_bytes = 4 * 2 * 8192;  // two 8 KB staging buffers for each of the four epilogue groups
+  std::vector<int4> none;
+  return launch(mB, mB, none, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, 128, true, true, &mO);
+}
+
 cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s) {
+  if (a.pair_stack) return tc_assemble_pair(a, s);
   // Fused multi-order assembly as one complex GEMM: rows = the N*N entries of the
   // entry-major split stack (K = all stored blocks), columns = the orders, whose
   // "signals" are their coefficient vectors over the stored blocks.

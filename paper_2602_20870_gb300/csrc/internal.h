@@ -36,6 +36,12 @@ struct fgfrft_plan_s {
   double min_gap_lo, min_gap_hi;  // bracket of min_{k not in I} |lambda_k + 1| (inf when r_neg1 = N)
   double neg1_tol;                // 0: adaptive classification
   bool real;           // F (hence every stored block) is real: tensor paths skip the imaginary planes
+  // pair stack (fg_pair_stack) for the fused multi-order assembly of split operators: built
+  // when F is real without a -1 eigenvalue (M_{-l} = M_l^T, M_0 = I), N % 128 == 0 and
+  // L_max % 16 == 0, in the entry-major storage's imaginary planes (unused for a real F)
+  bool pair;
+  __half* pairS;
+  int64_t pair_rows;
 };
 
 // Index of the stored block holding M_l (l in -L_max..L_max) and of P.
@@ -106,6 +112,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// The same test, suspending the thread until the phase completes or about hint_ns have passed
+// (the retry of a bounded wait: a waiting warp then takes no issue slots from working ones).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete, for at most
 // FG_WAIT_LIMIT_NS.  On timeout, record it in *status and return false.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
@@ -154,6 +174,23 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
+
+// Pair tiles (the pair stack of a real F without a -1 eigenvalue, N a multiple of 128): tile t
+// holds the 128 entries (i, 128 kt + r), r < 128, of the block-upper region kt >= i / 128, in
+// the order of row blocks I = i / 128, each 128 rows of nbt - I tiles (nbt = N / 128).
+__host__ __device__ __forceinline__ void pair_tile(int64_t t, int nbt, int& i, int& kt) {
+  int I = 0;
+  int64_t base = 0;
+  while (I < nbt - 1 && base + 128 * (int64_t)(nbt - I) <= t) {
+    base += 128 * (int64_t)(nbt - I);
+    ++I;
+  }
+  const int w = nbt - I;
+  const int64_t local = t - base;
+  i = 128 * I + (int)(local / w);
+  kt = I + (int)(local % w);
+}
+__host__ __device__ __forceinline__ int64_t pair_tiles(int nbt) { return 128 * (int64_t)nbt * (nbt + 1) / 2; }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -231,6 +268,14 @@ cudaError_t fg_store_block(int64_t N, const double2* M, bool conj_transpose, flo
 //   else (the tail):     T[4 * (Kp / 32) * planeT * 32 + (p * planeT + e) * (Kp % 32) + b % 32]
 cudaError_t fg_entry_major(const __half* f16, int nblk, int64_t N, int64_t Np, int64_t plane_elems, __half* T,
                            int64_t Kp, int64_t planeT, cudaStream_t s);
+// Pair stack of a real plan without a -1 eigenvalue (N % 128 == 0, L_max % 16 == 0): row
+// r < 128 of pair tile t = (i, kt) (pair_tile) holds, at column c < K2 = 2 L_max, split plane
+// p (0: hi, 1: lo) of M_l[i][128 kt + r], l = c - L_max for c < L_max, else c - L_max + 1 (M_0 = I
+// is not stored).  Tile-contiguous, as the MMA operand image a ring stage holds: tile t at
+// PS + t * 2 K2 * 128, then per 32-column chunk, per plane, 128 rows of 64 bytes whose 16-byte
+// pieces j sit at j ^ ((r >> 1) & 3) (the 64-byte swizzle); R = 128 * pair_tiles(N / 128) rows.
+cudaError_t fg_pair_stack(const __half* f16, int L_max, int64_t N, int64_t Np, int64_t plane_elems, __half* PS,
+                          int64_t R, cudaStream_t s);
 // One half-stack block (FP32 re/im planes of 64 x 64 swizzled tiles) from an FP64 matrix.
 cudaError_t fg_store_half(int64_t N, const double2* M, float* planes, int nt, int64_t hplane, cudaStream_t s);
 
@@ -302,3 +347,9 @@ cudaError_t fg_split_signals(const void* X, int64_t B, int64_t N, int64_t Np, in
 // launch's parameters, so the kernel does not wait on a read of the table.
 cudaError_t fg_coeff_planes(const double* alpha, int64_t A, int L, int L_max, int64_t Kp, __half* planes,
                             int* col_exp, cudaStream_t s, const double* alpha_host = nullptr);
+// Coefficient planes of the pair assembly (A <= 64 orders): [4][128][2 L_max], row a < A holding
+// c_l(alpha_a) and row 64 + a holding c_{-l}(alpha_a) at the pair stack's column of each power
+// l != 0 (zero for |l| > L), other rows zero; col_exp[0 .. 127] = FG_COEF_EXP; diag[a] = c_0(alpha_a)
+// * 2^(FG_SPLIT_SHIFT + FG_COEF_EXP).
+cudaError_t fg_coeff_planes_pair(const double* alpha, int64_t A, int L, int L_max, __half* planes, int* col_exp,
+                                 float* diag, cudaStream_t s, const double* alpha_host = nullptr);

@@ -284,6 +284,38 @@ __global__ void __launch_bounds__(256) entry_major_kernel(const __half* __restri
   }
 }
 
+// Pair stack (fg_pair_stack): 32 rows of one pair tile x 32 columns per CTA, transposed in
+// shared memory so the reads (along k of one row of M_l) and the writes (along the columns of
+// one pair row) are both contiguous.
+__global__ void __launch_bounds__(256) pair_stack_kernel(const __half* __restrict__ f16, int L_max, int nbt,
+                                                         int64_t Np, int64_t plane_elems, __half* __restrict__ PS,
+                                                         int64_t R) {
+  __shared__ __half tile[32][33];
+  const int64_t rho0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int p = blockIdx.z;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  int i = 0, kt = 0;
+  pair_tile(rho0 / 128, nbt, i, kt);
+  const int64_t k0 = 128 * (int64_t)kt + rho0 % 128;
+  for (int r = ty; r < 32; r += 8) {  // r: column offset, tx: row offset
+    const int c = c0 + r;
+    const int l = c < L_max ? c - L_max : c - L_max + 1;
+    const int64_t blk = L_max + l;
+    tile[r][tx] = f16[blk * 4 * plane_elems + (int64_t)p * plane_elems + (int64_t)i * Np + k0 + tx];
+  }
+  __syncthreads();
+  // tile t's image: [chunk][plane][128 rows x 32 halves], each row's 16-byte pieces placed as
+  // the 64-byte swizzle puts them in shared memory (piece j of row r at j ^ ((r >> 1) & 3))
+  const int nch = L_max / 16;  // K2 / 32
+  const int64_t t = rho0 / 128;
+  __half* img = PS + ((t * nch + blockIdx.y) * 2 + p) * (128 * 32);
+  for (int r = ty; r < 32; r += 8) {  // r: row offset, tx: column offset
+    const int rr = (int)(rho0 % 128) + r;
+    img[rr * 32 + (tx ^ (((rr >> 1) & 3) << 3))] = tile[tx][r];
+  }
+}
+
 // out[0] = sum of Im(F_ik)^2 (one block, fixed order): zero iff F is real.
 __global__ void __launch_bounds__(1024) zimag_sq_kernel(int64_t total, const double2* __restrict__ F, double* out) {
   __shared__ double red[32];
@@ -369,6 +401,15 @@ cudaError_t fg_store_block(int64_t N, const double2* M, bool conj_transpose, flo
 cudaError_t fg_store_half(int64_t N, const double2* M, float* planes, int nt, int64_t hplane, cudaStream_t s) {
   dim3 grid((unsigned)nt, (unsigned)nt);
   store_half_kernel<<<grid, 256, 0, s>>>(N, M, nt, planes, hplane);
+  fg_note_launch(FGFRFT_KC_OFFLINE);
+  return cudaGetLastError();
+}
+
+cudaError_t fg_pair_stack(const __half* f16, int L_max, int64_t N, int64_t Np, int64_t plane_elems, __half* PS,
+                          int64_t R, cudaStream_t s) {
+  if (N % 128 || L_max % 16 || L_max < 16 || R != pair_tiles((int)(N / 128)) * 128) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)(R / 32), (unsigned)(L_max / 16), 2);
+  pair_stack_kernel<<<grid, 256, 0, s>>>(f16, L_max, (int)(N / 128), Np, plane_elems, PS, R);
   fg_note_launch(FGFRFT_KC_OFFLINE);
   return cudaGetLastError();
 }

@@ -174,6 +174,46 @@ __global__ void __launch_bounds__(256) coeff_planes_kernel(const double* __restr
   }
 }
 
+// Pair assembly coefficients (fg_coeff_planes_pair), one CTA per row b < 128 of the resident
+// operator: b = a < A gives order a's c_l, b = 64 + a its mirror coefficients c_{-l}, at column
+// c of the pair stack (power l = c - L_max below L_max, c - L_max + 1 from it); the same FP32
+// evaluation as coeff_planes_kernel.
+__global__ void __launch_bounds__(128) coeff_planes_pair_kernel(const double* __restrict__ alpha,
+                                                                const CoefOrders orders, int L, int L_max, int64_t A,
+                                                                __half* __restrict__ planes,
+                                                                int* __restrict__ col_exp, float* __restrict__ diag) {
+  const int b = blockIdx.x;
+  const int64_t a_idx = b < 64 ? b : b - 64;
+  const bool live = a_idx < A;
+  const double a = live ? (alpha ? alpha[a_idx] : orders.a[a_idx]) : 0.0;
+  const double n0d = rint(a);
+  const float d = (float)(a - n0d);
+  const float sgn0 = fmod(n0d, 2.0) != 0.0 ? -1.f : 1.f;
+  const float sa = sgn0 * sinpif(d);
+  const float pi_f = 3.14159265358979323846f;
+  auto coef = [&](int l) -> float {  // c_l(a) for |l| <= L, else 0
+    if (l > L || l < -L) return 0.f;
+    const float dl = d + (float)(n0d - (double)l);
+    return dl == 0.f ? 1.f : ((l & 1) ? -sa : sa) / (pi_f * dl);
+  };
+  if (threadIdx.x == 0) {
+    col_exp[b] = FG_COEF_EXP;
+    if (live && b < 64) diag[a_idx] = coef(0) * (float)(1 << (FG_SPLIT_SHIFT + FG_COEF_EXP));
+  }
+  const int64_t K2 = 2 * (int64_t)L_max;
+  __half* r_hi = planes + (int64_t)b * K2;
+  for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < K2; k0 += 4 * (int64_t)blockDim.x) {
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = (int)(k0 + u);
+      const int l = c < L_max ? c - L_max : c - L_max + 1;
+      v[u] = make_float2(live ? coef(b < 64 ? l : -l) : 0.f, 0.f);
+    }
+    split_store4(v, FG_COEF_EXP, r_hi, 128 * K2, k0);  // K2 is a multiple of 32
+  }
+}
+
 constexpr int GR_CHUNK = 4096;
 
 // level 1: partial[j][chunk] = Re sum_{i in chunk} conj(G_ji) D_ji   (FP64)
@@ -480,5 +520,19 @@ cudaError_t fg_coeff_planes(const double* alpha, int64_t A, int L, int L_max, in
     alpha = nullptr;
   }
   coeff_planes_kernel<<<(unsigned)A, 256, 0, s>>>(alpha, ord, L, L_max, A, Kp, planes, col_exp);
+  return cudaGetLastError();
+}
+
+cudaError_t fg_coeff_planes_pair(const double* alpha, int64_t A, int L, int L_max, __half* planes, int* col_exp,
+                                 float* diag, cudaStream_t s, const double* alpha_host) {
+  if (A <= 0 || A > 64 || L_max % 16 || L > L_max) return cudaErrorInvalidValue;
+  FgTimed timed(FGFRFT_KC_COEFFS, s);
+  fg_note_launch(FGFRFT_KC_COEFFS);
+  CoefOrders ord{};
+  if (alpha_host) {
+    for (int64_t i = 0; i < A; ++i) ord.a[i] = alpha_host[i];
+    alpha = nullptr;
+  }
+  coeff_planes_pair_kernel<<<128, 128, 0, s>>>(alpha, ord, L, L_max, A, planes, col_exp, diag);
   return cudaGetLastError();
 }

@@ -35,6 +35,8 @@ struct TcGroupedArgs {
   bool x_split_done;       // Xs, col_exp and bimag already hold this X (a second GEMM on it)
   bool x_real;             // X is real float32
   bool y_real;             // write only the real parts (the caller knows the products are real)
+  bool pair;               // Qs came from the pair assembly: left of each row tile's diagonal
+                           // block, Q_g[i][k] is read from planes 2, 3 at (k, i) (real_a only)
 };
 cudaError_t fg_tc_grouped_apply(const TcGroupedArgs& a, cudaStream_t s);
 // Column-tile width of the grouped GEMM (256 for real operators, else 128) and its tile table:
@@ -94,6 +96,14 @@ struct TcAssembleArgs {
   bool real_a;                // the stored blocks are real (real F)
   bool skip_im;               // split output whose imaginary part is zero (real F, no -1 eigenvalue)
   bool re_only;               // real blocks and a real result: form only the real accumulator
+  // pair assembly (real F without a -1 eigenvalue, split output, A <= 64, N % 128 == 0):
+  // pair_stack != NULL selects it; Cs is then [4][128][K2] (rows a: c_l(alpha_a), rows 64 + a:
+  // c_{-l}(alpha_a), over the stored powers l != 0) and Qs receives Q_a in planes 0, 1 on and
+  // right of the diagonal blocks, Q_a^T in planes 2, 3 left of them (see fg_pair_stack)
+  const __half* pair_stack;   // chunk-major [2 planes][K2 / 32][pair_rows][32]
+  int64_t pair_rows;          // 128 * (pair tiles)
+  int64_t K2;                 // 2 L_max
+  const float* diag;          // [A]: c_0(alpha_a) at the accumulator scale
 };
 cudaError_t fg_tc_assemble(const TcAssembleArgs& a, cudaStream_t s);
 size_t fg_tc_assemble_scratch_bytes(int64_t entries, int64_t A);

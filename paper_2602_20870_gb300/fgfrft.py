@@ -45,6 +45,7 @@ SIGNATURES = {
     "fgfrft_plan_status": (_i32, [_vp, _vp]),
     "fgfrft_plan_destroy": (_i32, [_vp]),
     "fgfrft_plan_real": (_i32, [_vp]),
+    "fgfrft_plan_pair": (_i32, [_vp]),
     "fgfrft_work_bytes": (_sz, [_vp, _i32, _vp, _i64, _i32, _i32]),
     "fgfrft_assemble": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _sz, _vp]),
     "fgfrft_apply": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp, _sz, _vp]),
@@ -222,6 +223,8 @@ class Plan:
         self.r_neg1, self.proj_residual, self.squarings, self.plan_bytes = rn.value, res.value, sq.value, pb.value
         self.min_gap = (gap[0], gap[1])
         self.real = lib.fgfrft_plan_real(h) == 1
+        # the fused multi-order assembly reads the pair stack (real F without -1 eigenvalue)
+        self.pair = lib.fgfrft_plan_pair(h) == 1
         # one work buffer per CUDA stream: calls on different streams never share scratch
         self._works = {}
 
