@@ -231,7 +231,8 @@ int fgfrft_plan_status(fgfrft_plan p, void* stream);
 int fgfrft_plan_real(fgfrft_plan p);
 
 /* 1 if the plan holds the pair stack: F real with no eigenvalue -1 (r_-1 = 0),
- * FGFRFT_STORE_ENTRY_F16, N a multiple of 128 and L_max a multiple of 16 (at most 80).
+ * FGFRFT_STORE_ENTRY_F16, N a multiple of 128, L_max a multiple of 16 and the pair launch
+ * fits in the device's shared memory (L_max <= 64 on GB300).
  * Then M_{-l} = M_l^T (F^{-1} = F^T; Prop. 2) and M_0 = P_c = I, so the fused multi-order
  * assembly of split operators (the assembled path of fgfrft_apply) reads one row of the
  * 2 L_max powers l != 0 per entry pair {(i, k), (k, i)} (i/128 <= k/128), about half the

@@ -762,7 +762,7 @@ int fgfrft_precompute(const double* F_dev, int64_t N, int L_max, int storage, co
   // imaginary planes of the entry-major copy's full chunks (2 (Kp / 32) planeT 32 entries >=
   // 2 (2 L_max) rows, since 32 (Kp / 32) = 2 L_max for L_max % 16 == 0 and rows <= planeT)
   p->pair = false;
-  if (p->f16T && p->real && p->r_neg1 == 0 && N % 128 == 0 && L_max % 16 == 0 && L_max <= 80) {
+  if (p->f16T && p->real && p->r_neg1 == 0 && N % 128 == 0 && fg_tc_pair_fits(L_max)) {
     const int64_t rows = 128 * pair_tiles((int)(N / 128));
     const int64_t nfull = p->Kp / 32;
     if (2 * (int64_t)L_max * rows <= 32 * nfull * p->planeT) {

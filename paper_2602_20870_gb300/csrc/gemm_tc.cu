@@ -144,8 +144,10 @@ struct TcParams {
   const uint8_t* a_img;
   // pair assembly output through shared memory: each epilogue group stages a 16-column chunk
   // (16 orders x 2 planes x 128 entries, 8 KB) and one 4-D tensor store (tmT: {k, i, plane,
-  // order}) writes it; out_bytes = the staging area (two buffers per group), 0: direct stores
+  // order}) writes it; out_bytes = the staging area (out_bufs 8 KB buffers per group: two when
+  // they fit beside two ring stages, else one), 0: direct stores
   int out_bytes;
+  int out_bufs;
   // grouped GEMM over pair-structured operators: k-chunks left of the row tile's diagonal
   // block come from the transposed store (planes 2, 3 of the group), read MN-major
   int pair_lower;
@@ -368,6 +370,8 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, uint32_t sr
 }
 // wait until at most one of this thread's bulk stores still reads shared memory
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// wait until none of this thread's bulk stores still reads shared memory
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // wait until every bulk store of this thread has completed
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -688,7 +692,8 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
     // staged pair output: the group's first warp, lane 0, issues its tensor stores
     const bool staged = RB && out_bytes > 0 && pingpong;
     const bool leader = staged && warp == TC_EPI_WARP0 + 4 * grp && lane == 0;
-    const uint32_t gbuf = smem_u32(obuf) + (uint32_t)grp * 2u * 8192u;
+    const uint32_t obufs = p.out_bufs == 1 ? 1u : 2u;
+    const uint32_t gbuf = smem_u32(obuf) + (uint32_t)grp * obufs * 8192u;
     uint32_t nstaged = 0;
     for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++li) {
       const bool mine = !pingpong || (int)(li % NGRP) == grp;
@@ -769,8 +774,13 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
           if (staged) {
             // through shared memory: this buffer's previous store must have read it, then
             // the group fills it and one tensor store writes the 16 orders x 2 planes
-            const uint32_t buf = gbuf + (nstaged & 1u) * 8192u;
-            if (leader) bulk_wait_read1();
+            const uint32_t buf = gbuf + (obufs == 2u ? (nstaged & 1u) * 8192u : 0u);
+            if (leader) {
+              if (obufs == 2u)
+                bulk_wait_read1();
+              else
+                bulk_wait_read0();
+            }
             grp_bar(grp);
             stage_split16(reinterpret_cast<const uint32_t(&)[16]>(vr), p.uscale, buf, row);
             fence_proxy_async_smem();
@@ -1042,6 +1052,7 @@ bool fg_tc_available() {
 
 int64_t fg_tc_signal_rows(int64_t B, int64_t) { return B; }
 
+
 size_t fg_tc_scratch_bytes(int64_t N, int64_t B, int64_t groups, int nblk) {
   const int64_t row_tiles = (N + TC_BM - 1) / TC_BM;
   const int64_t col_tiles = (B + 63) / 64 + groups;  // each group may add a ragged tile (tiles >= 64 wide)
@@ -1179,6 +1190,23 @@ int fg_tc_stacked_splits(int64_t N, int64_t B, int nblk) {
   return (nblk + bps - 1) / bps;
 }
 
+// Staging buffers per epilogue group of the pair launch for this L_max: 2 when they fit beside
+// two ring stages and the resident coefficients, else 1, else 0 (the launch does not fit).
+static int pair_out_bufs(int L_max) {
+  const int nch = 2 * L_max / TC_KC;
+  const int stage = nch * 2 * TC_BM * TC_KC * 2;         // A hi, lo per chunk
+  const int res = nch * 2 * 128 * TC_KC * 2;             // the resident coefficients, 2 planes
+  const int avail = smem_optin() - 1024 - (int)sizeof(TcCtl) - res;
+  for (int b = 2; b >= 1; --b)
+    if (avail - 4 * b * 8192 >= TC_MIN_STAGES * stage) return b;
+  return 0;
+}
+
+bool fg_tc_pair_fits(int L_max) {
+  return fg_tc_available() && L_max % 16 == 0 && L_max >= 16 && 2 * L_max / TC_KC <= TC_RB_MAXCH &&
+         pair_out_bufs(L_max) > 0;
+}
+
 // Pair assembly (real F without a -1 eigenvalue): one GEMM row per entry pair (i, k) of the
 // block-upper region, K = the 2 L_max powers M_l, l != 0 (M_0 = I and P = 0 are not stored);
 // columns: the orders' coefficients c_l and, 64 columns on, the mirror coefficients c_{-l},
@@ -1227,7 +1255,9 @@ static cudaError_t tc_assemble_pair(const TcAssembleArgs& a, cudaStream_t s) {
   p.pair_nbt = (int)(a.N / 128);
   p.pair_A = (int)a.A;
   p.diag = a.diag;
-  p.out_bytes = 4 * 2 * 8192;  // two 8 KB staging buffers for each of the four epilogue groups
+  p.out_bufs = pair_out_bufs((int)(a.K2 / 2));
+  if (p.out_bufs == 0) return cudaErrorNotSupported;
+  p.out_bytes = 4 * p.out_bufs * 8192;  // 8 KB staging buffers for each of the four epilogue groups
   std::vector<int4> none;
   return launch(mB, mB, none, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, 128, true, true, &mO);
 }

@@ -6,6 +6,9 @@
 
 // True when the tcgen05 kernels are compiled in and the current device is sm_103.
 bool fg_tc_available();
+// True when the pair assembly's launch (K = 2 L_max powers, resident coefficients, staging
+// buffers, two ring stages) fits in the shared memory of the current device.
+bool fg_tc_pair_fits(int L_max);
 // Rows of the signal split planes for B signals in the given number of groups
 // (padded so that every TMA box row stays inside the buffer).
 int64_t fg_tc_signal_rows(int64_t B, int64_t groups);

@@ -3,9 +3,10 @@ plan keeps one row of the 2 L_max powers M_l, l != 0, per entry pair (i, k) with
 i/128 <= k/128; the fused multi-order assembly forms Q[i][k] from c_l and Q[k][i] from
 c_{-l} (M_{-l} = M_l^T, Prop. 2; M_0 = I adds c_0 on the diagonal; Def. 1), and the grouped
 GEMM reads the operator left of each row tile's diagonal block from its transposed store.
-Cases span one, two and three 128-row blocks (diagonal blocks only; mirrors), ragged order
-groups, more than 64 groups (two assembly passes), integer orders, L below L_max, complex
-and real signals.  Bars: the split-precision bar on relative Frobenius error per group, and
+Cases span one, two and three 128-row blocks (diagonal blocks only; mirrors), L_max = 16 ... 64
+(one to four 32-power chunks; at 64 the launch keeps one output staging buffer per epilogue
+group), ragged order groups, more than 64 groups (two assembly passes), integer orders, L below
+L_max, complex and real signals.  Bars: the split-precision bar on relative Frobenius error per group, and
 the same on each column's maximum relative error (a wrong tile or a missed mirror shows up
 in the columns it touches)."""
 import numpy as np
@@ -38,16 +39,17 @@ def real_gft_without_minus_one(n, seed):
     return F
 
 
-CASES = [(128, 16, 11), (256, 32, 12), (384, 16, 13)]
+CASES = [(128, 16, 11), (256, 32, 12), (384, 16, 13), (256, 48, 14), (256, 64, 15)]
+IDS = [f"N{n}-Lmax{L}" for n, L, _ in CASES]
 
 
 @pytest.fixture(scope="module")
 def plans(FG):
     out = {}
-    for n, L_max, seed in CASES:
+    for (n, L_max, seed), name in zip(CASES, IDS):
         F = real_gft_without_minus_one(n, seed)
         plan = FG.Plan(F, L_max)
-        out[n] = (F, plan)
+        out[name] = (F, plan)
     return out
 
 
@@ -63,16 +65,17 @@ def check_groups(Y, X, F, alpha, L, starts, counts):
         assert col.max() < TOL_SPLIT, (s, c, float(col.max()))
 
 
-@pytest.mark.parametrize("n", [c[0] for c in CASES])
-def test_plan_builds_the_pair_stack(plans, n):
-    F, plan = plans[n]
+@pytest.mark.parametrize("name", IDS)
+def test_plan_builds_the_pair_stack(plans, name):
+    F, plan = plans[name]
     assert plan.real and plan.r_neg1 == 0 and plan.pair
 
 
-@pytest.mark.parametrize("n", [c[0] for c in CASES])
+@pytest.mark.parametrize("name", IDS)
 @pytest.mark.parametrize("L_off", [0, 5])
-def test_pair_assembly_groups_match_oracle(FG, plans, n, L_off):
-    F, plan = plans[n]
+def test_pair_assembly_groups_match_oracle(FG, plans, name, L_off):
+    F, plan = plans[name]
+    n = F.shape[0]
     L = plan.L_max - L_off
     rng = np.random.default_rng(100 + n + L_off)
     counts = [1, 17, 64, 3, 40, 9]
@@ -91,7 +94,7 @@ def test_pair_assembly_groups_match_oracle(FG, plans, n, L_off):
 
 
 def test_more_than_64_orders_two_passes(FG, plans):
-    F, plan = plans[256]
+    F, plan = plans["N256-Lmax32"]
     L = plan.L_max
     rng = np.random.default_rng(7)
     counts = [2] * 70 + [5]  # 71 order groups: two passes of the pair assembly
@@ -105,7 +108,7 @@ def test_more_than_64_orders_two_passes(FG, plans):
 
 
 def test_real_signals_and_outputs(FG, plans):
-    F, plan = plans[384]
+    F, plan = plans["N384-Lmax16"]
     L = plan.L_max
     rng = np.random.default_rng(9)
     counts = [30, 1, 33]
