@@ -148,6 +148,7 @@ struct TcParams {
   // they fit beside two ring stages, else one), 0: direct stores
   int out_bytes;
   int out_bufs;
+  int out_pairs;      // 1: two 16-order chunks per tensor store (one 16 KB buffer per group)
   // grouped GEMM over pair-structured operators: k-chunks left of the row tile's diagonal
   // block come from the transposed store (planes 2, 3 of the group), read MN-major
   int pair_lower;
@@ -693,7 +694,8 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
     const bool staged = RB && out_bytes > 0 && pingpong;
     const bool leader = staged && warp == TC_EPI_WARP0 + 4 * grp && lane == 0;
     const uint32_t obufs = p.out_bufs == 1 ? 1u : 2u;
-    const uint32_t gbuf = smem_u32(obuf) + (uint32_t)grp * obufs * 8192u;
+    const bool opairs = p.out_pairs != 0;
+    const uint32_t gbuf = smem_u32(obuf) + (uint32_t)grp * (opairs ? 16384u : obufs * 8192u);
     uint32_t nstaged = 0;
     for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++li) {
       const bool mine = !pingpong || (int)(li % NGRP) == grp;
@@ -719,7 +721,7 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
       // the same position of the transposed store unless the tile is in a diagonal block
       bool mirror_ok = false, diag_lane = false;
       int pi = 0, pkt = 0;
-      if (p.pair_nbt) {
+      if (p.pair_nbt && mine) {
         pair_tile(tile.x, p.pair_nbt, pi, pkt);
         qoff = (int64_t)pi * p.qNp + 128 * (int64_t)pkt + row;
         mirror_ok = pkt != pi / 128;
@@ -737,8 +739,64 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
         }
         fence_tc_after();
         const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + buf * acc_w;
+        if (staged) {
+          // the pair launch's output: chunks of 16 columns, the first 64 the orders' Q[i][k],
+          // the rest their mirrors (skipped in a diagonal block); every test here is uniform
+          // over the group, and only the warp holding the diagonal entry adds c_0
+          const bool diag_warp = __any_sync(0xffffffffu, diag_lane);
 #pragma unroll 1
-        for (int cc = pingpong ? 0 : grp; cc < TC_BN / CW; cc += pingpong ? 1 : NGRP) {
+          for (int cc = 0; cc < TC_BN / CW; ++cc) {
+            const bool mir = cc >= 4;
+            const int jo = (cc & 3) * CW;
+            if (jo >= p.pair_A || (mir && !mirror_ok)) continue;
+            uint32_t vr[CW];
+            __syncwarp();
+            tmem_ld(base + cc * CW, vr);
+            tmem_wait_ld();
+            if (diag_warp && !mir) {
+              if (diag_lane) {
+#pragma unroll
+                for (int c = 0; c < CW; ++c)
+                  if (jo + c < p.pair_A) vr[c] = __float_as_uint(__uint_as_float(vr[c]) + __ldg(p.diag + jo + c));
+              }
+              __syncwarp();
+            }
+            if (opairs) {
+              // two chunks (32 orders) per tensor store: the first half of a pair waits until
+              // the group's buffer has been read by the previous store; the store follows the
+              // pair's last chunk in range (orders past A are outside the tensor, not written)
+              const int h = cc & 1;
+              if (h == 0) {
+                if (leader) bulk_wait_read0();
+                grp_bar(grp);
+              }
+              stage_split16(reinterpret_cast<const uint32_t(&)[16]>(vr), p.uscale, gbuf + (uint32_t)h * 8192u, row);
+              if (h == 1 || jo + CW >= p.pair_A) {
+                fence_proxy_async_smem();
+                grp_bar(grp);
+                if (leader) tma_store_4d(&tmT, gbuf, 128 * pkt, pi, mir ? 2 : 0, jo - CW * h);
+              }
+            } else {
+              // one chunk per store: this buffer's previous store must have read it, then the
+              // group fills it and one tensor store writes the 16 orders x 2 planes
+              const uint32_t sbuf = gbuf + (obufs == 2u ? (nstaged & 1u) * 8192u : 0u);
+              if (leader) {
+                if (obufs == 2u)
+                  bulk_wait_read1();
+                else
+                  bulk_wait_read0();
+              }
+              grp_bar(grp);
+              stage_split16(reinterpret_cast<const uint32_t(&)[16]>(vr), p.uscale, sbuf, row);
+              fence_proxy_async_smem();
+              grp_bar(grp);
+              if (leader) tma_store_4d(&tmT, sbuf, 128 * pkt, pi, mir ? 2 : 0, jo);
+              ++nstaged;
+            }
+          }
+        }
+#pragma unroll 1
+        for (int cc = pingpong ? 0 : grp; !staged && cc < TC_BN / CW; cc += pingpong ? 1 : NGRP) {
           int j0 = tile.z + cc * CW;
           if (j0 >= tile.w) break;  // uniform: no column of this chunk is in range
           int ncol = min(CW, tile.w - j0);
@@ -771,23 +829,7 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
             for (int c = 0; c < CW; ++c)
               if (c < ncol) vr[c] = __float_as_uint(__uint_as_float(vr[c]) + __ldg(p.diag + j0 + c));
           }
-          if (staged) {
-            // through shared memory: this buffer's previous store must have read it, then
-            // the group fills it and one tensor store writes the 16 orders x 2 planes
-            const uint32_t buf = gbuf + (obufs == 2u ? (nstaged & 1u) * 8192u : 0u);
-            if (leader) {
-              if (obufs == 2u)
-                bulk_wait_read1();
-              else
-                bulk_wait_read0();
-            }
-            grp_bar(grp);
-            stage_split16(reinterpret_cast<const uint32_t(&)[16]>(vr), p.uscale, buf, row);
-            fence_proxy_async_smem();
-            grp_bar(grp);
-            if (leader) tma_store_4d(&tmT, buf, 128 * pkt, pi, mir ? 2 : 0, j0);
-            ++nstaged;
-          } else if (!row_ok) {
+          if (!row_ok) {
             // rows past the end: nothing to store
           } else if (split_out) {
             // value * 2^FG_SPLIT_SHIFT as fp16 hi + lo, four planes per column (a mirror
@@ -1201,6 +1243,13 @@ static int pair_out_bufs(int L_max) {
     if (avail - 4 * b * 8192 >= TC_MIN_STAGES * stage) return b;
   return 0;
 }
+// Two chunks per tensor store (a 16 KB buffer per group) when that keeps four ring stages.
+static bool pair_out_pairs(int L_max) {
+  const int nch = 2 * L_max / TC_KC;
+  const int stage = nch * 2 * TC_BM * TC_KC * 2;
+  const int res = nch * 2 * 128 * TC_KC * 2;
+  return smem_optin() - 1024 - (int)sizeof(TcCtl) - res - 4 * 16384 >= 4 * stage;
+}
 
 bool fg_tc_pair_fits(int L_max) {
   return fg_tc_available() && L_max % 16 == 0 && L_max >= 16 && 2 * L_max / TC_KC <= TC_RB_MAXCH &&
@@ -1225,7 +1274,7 @@ static cudaError_t tc_assemble_pair(const TcAssembleArgs& a, cudaStream_t s) {
     if (!enc) return cudaErrorInvalidValue;
     cuuint64_t dims[4] = {(cuuint64_t)a.N, (cuuint64_t)a.N, 4, (cuuint64_t)a.A};
     cuuint64_t strides[3] = {(cuuint64_t)a.Np * 2, (cuuint64_t)a.plane_elems * 2, (cuuint64_t)a.plane_elems * 8};
-    cuuint32_t box[4] = {128, 1, 2, 16};
+    cuuint32_t box[4] = {128, 1, 2, pair_out_pairs((int)(a.K2 / 2)) ? 32u : 16u};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     if (enc(&mO, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, a.Qs, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
@@ -1257,7 +1306,10 @@ static cudaError_t tc_assemble_pair(const TcAssembleArgs& a, cudaStream_t s) {
   p.diag = a.diag;
   p.out_bufs = pair_out_bufs((int)(a.K2 / 2));
   if (p.out_bufs == 0) return cudaErrorNotSupported;
-  p.out_bytes = 4 * p.out_bufs * 8192;  // 8 KB staging buffers for each of the four epilogue groups
+  p.out_pairs = pair_out_pairs((int)(a.K2 / 2)) ? 1 : 0;
+  // staging buffers of the four epilogue groups: one 16 KB buffer (two chunks per store), or
+  // out_bufs 8 KB buffers
+  p.out_bytes = p.out_pairs ? 4 * 16384 : 4 * p.out_bufs * 8192;
   std::vector<int4> none;
   return launch(mB, mB, none, p, a.scratch, a.scratch_bytes, s, FGFRFT_KC_ASSEMBLE_MULTI, 128, true, true, &mO);
 }
