@@ -417,7 +417,8 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
   const int nst = min(TC_MAXST, (p.smem_bytes - (int)sizeof(TcCtl) - res_bytes - out_bytes) / stage_bytes);
   // a launch sized for real signals whose split reports an imaginary part (or any other
   // mismatch of the host's sizing): record it and return before anything is set up
-  if (nst < 1 || (p.stage_bytes && !tail16 && cps * chunk_bytes > p.stage_bytes)) {
+  if (nst < 1 || (p.stage_bytes && !tail16 && cps * chunk_bytes > p.stage_bytes) ||
+      (p.pair_nbt && (!RB || out_bytes == 0))) {
     if (threadIdx.x == 0) atomicOr(p.status, FG_STATUS_LAUNCH_MISMATCH);
     return;
   }
@@ -797,16 +798,9 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
         }
 #pragma unroll 1
         for (int cc = pingpong ? 0 : grp; !staged && cc < TC_BN / CW; cc += pingpong ? 1 : NGRP) {
-          int j0 = tile.z + cc * CW;
+          const int j0 = tile.z + cc * CW;
           if (j0 >= tile.w) break;  // uniform: no column of this chunk is in range
-          int ncol = min(CW, tile.w - j0);
-          bool mir = false;
-          if (p.pair_nbt) {  // columns 64 + j hold the mirror of order j (uniform per warp)
-            mir = j0 >= 64;
-            if (mir) j0 -= 64;
-            ncol = min(CW, p.pair_A - j0);
-            if (ncol <= 0 || (mir && !mirror_ok)) continue;
-          }
+          const int ncol = min(CW, tile.w - j0);
           uint32_t vr[CW], vi[CW];
           __syncwarp();  // tcgen05.ld is warp-collective: the whole warp converged
           tmem_ld(base + cc * CW, vr);
@@ -824,18 +818,12 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
               vi[c] = 0u;
             }
           }
-          if (diag_lane && !mir) {  // Q[i][i] += c_0 (M_0 = I is not stored)
-#pragma unroll
-            for (int c = 0; c < CW; ++c)
-              if (c < ncol) vr[c] = __float_as_uint(__uint_as_float(vr[c]) + __ldg(p.diag + j0 + c));
-          }
           if (!row_ok) {
             // rows past the end: nothing to store
           } else if (split_out) {
-            // value * 2^FG_SPLIT_SHIFT as fp16 hi + lo, four planes per column (a mirror
-            // column goes to planes 2, 3)
+            // value * 2^FG_SPLIT_SHIFT as fp16 hi + lo, four planes per column
             if (p.uscale != 0.f)
-              split_out_cols<true, CW>(vr, vi, p, sm.scale, cc, j0, ncol, mir ? qoff + 2 * p.qplane : qoff);
+              split_out_cols<true, CW>(vr, vi, p, sm.scale, cc, j0, ncol, qoff);
             else
               split_out_cols<false, CW>(vr, vi, p, sm.scale, cc, j0, ncol, qoff);
           } else if (p.coef == nullptr && p.y_real) {
