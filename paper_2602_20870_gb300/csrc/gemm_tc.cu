@@ -852,28 +852,43 @@ __global__ void __launch_bounds__(TcCfg<BN, RB, RA, KC>::THREADS, 1)
             const float2* cfp = p.coef + (int64_t)b * p.ldcoef + j0;
             const float2* cdp = p.D ? p.coefd + (int64_t)b * p.ldcoef + j0 : nullptr;
             const bool first = b == br.x;
+            // groups of 4 columns: the partial sums of a group are loaded first and then
+            // updated and stored, so their loads are in flight together (a load after the
+            // previous column's store would wait for it: the compiler cannot tell that they do
+            // not alias).  Only the stacked launches (streamed B) take this path.
+            if constexpr (!RB) {
+              constexpr int CG = 4;
 #pragma unroll
-            for (int c = 0; c < CW; ++c) {
-              if (c < ncol) {
-                const float sc = sm.scale[cc * CW + c];
-                const float tr = __uint_as_float(vr[c]) * sc, ti = __uint_as_float(vi[c]) * sc;
-                if (yp) {
-                  const float2 cf = __ldg(cfp + c);
-                  float2 y = first ? make_float2(0.f, 0.f) : *yp;
-                  y.x = fmaf(cf.x, tr, fmaf(-cf.y, ti, y.x));
-                  y.y = fmaf(cf.x, ti, fmaf(cf.y, tr, y.y));
-                  *yp = y;
+              for (int c0 = 0; c0 < CW; c0 += CG) {
+                float2 yv[CG], dv[CG];
+#pragma unroll
+                for (int u = 0; u < CG; ++u) {
+                  const bool ld = c0 + u < ncol && !first;
+                  yv[u] = yp && ld ? yp[(int64_t)(c0 + u) * p.rows] : make_float2(0.f, 0.f);
+                  dv[u] = dp && ld ? dp[(int64_t)(c0 + u) * p.rows] : make_float2(0.f, 0.f);
                 }
-                if (dp) {
-                  const float2 cd = __ldg(cdp + c);
-                  float2 d = first ? make_float2(0.f, 0.f) : *dp;
-                  d.x = fmaf(cd.x, tr, fmaf(-cd.y, ti, d.x));
-                  d.y = fmaf(cd.x, ti, fmaf(cd.y, tr, d.y));
-                  *dp = d;
+#pragma unroll
+                for (int u = 0; u < CG; ++u) {
+                  const int c = c0 + u;
+                  if (c >= ncol) continue;
+                  const float sc = sm.scale[cc * CW + c];
+                  const float tr = __uint_as_float(vr[c]) * sc, ti = __uint_as_float(vi[c]) * sc;
+                  if (yp) {
+                    const float2 cf = __ldg(cfp + c);
+                    float2 y = yv[u];
+                    y.x = fmaf(cf.x, tr, fmaf(-cf.y, ti, y.x));
+                    y.y = fmaf(cf.x, ti, fmaf(cf.y, tr, y.y));
+                    yp[(int64_t)c * p.rows] = y;
+                  }
+                  if (dp) {
+                    const float2 cd = __ldg(cdp + c);
+                    float2 d = dv[u];
+                    d.x = fmaf(cd.x, tr, fmaf(-cd.y, ti, d.x));
+                    d.y = fmaf(cd.x, ti, fmaf(cd.y, tr, d.y));
+                    dp[(int64_t)c * p.rows] = d;
+                  }
                 }
               }
-              if (yp) yp += p.rows;
-              if (dp) dp += p.rows;
             }
           }
         }
